@@ -1,0 +1,273 @@
+"""RASTER oracle -- TEST INFRASTRUCTURE ONLY.
+
+Python access to the plain single-threaded CPU oracle in ``raster_oracle.cpp``
+(Alg. 1 of the paper, written out).  Only ``tests/``, the package's smoke check
+and the benchmark's CPU-baseline leg may import this module; the CUDA library
+and its binding never do.
+
+Also holds two independent restatements used to pin the oracle on tiny inputs:
+``brute_force`` (all-pairs Chebyshev adjacency + union-find, a different
+algorithm from the oracle's neighbour search) and ``project_exact`` (exact
+rational arithmetic, then IEEE round-to-nearest, then floor).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "raster_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "_build", "libraster_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+E_RANGE = 2
+NOISE = np.iinfo(np.int64).min
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle: -O2, no fused multiply-add, no fast-math."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        compile_source(_SRC, tmp)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle source file (the real one, or a deliberately broken
+    copy made by a test) with the oracle's flags."""
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", src, "-o", out])
+    return out
+
+
+def load_library(path: str):
+    """Load an oracle shared library and declare its entry points."""
+    L = ctypes.CDLL(path)
+    _declare(L)
+    return L
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = load_library(_LIB_PATH)
+    return _lib
+
+
+def _declare(L):
+    vp, i64, u32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+    L.oracle_create.restype = vp
+    L.oracle_create.argtypes = [dbl, u32, u32]
+    L.oracle_free.argtypes = [vp]
+    L.oracle_add.restype = ctypes.c_int
+    L.oracle_add.argtypes = [vp, vp, i64]
+    L.oracle_finish.restype = ctypes.c_int
+    L.oracle_finish.argtypes = [vp]
+    for name in ("oracle_points", "oracle_n_tiles", "oracle_n_significant", "oracle_n_kept",
+                 "oracle_n_clusters"):
+        getattr(L, name).restype = i64
+        getattr(L, name).argtypes = [vp]
+    L.oracle_status.restype = ctypes.c_int
+    L.oracle_status.argtypes = [vp]
+    L.oracle_copy_tiles.argtypes = [vp, vp, vp]
+    L.oracle_copy_kept.argtypes = [vp, vp, vp, vp]
+    L.oracle_labels.restype = ctypes.c_int
+    L.oracle_labels.argtypes = [vp, vp, i64, vp]
+    L.oracle_project.argtypes = [vp, i64, dbl, vp, vp]
+    L.oracle_count_keys.argtypes = [vp, i64, dbl, vp, i64, vp]
+
+
+def scale_of(precision: float) -> float:
+    """s = 10^precision as one double: exact for integer precisions 0..22,
+    otherwise the host C library's pow(10, precision)."""
+    if precision == int(precision) and 0 <= precision <= 22:
+        return float(10 ** int(precision))
+    return 10.0 ** float(precision)
+
+
+def _xy(xy) -> np.ndarray:
+    a = np.ascontiguousarray(xy, dtype=np.float64)
+    assert a.ndim == 2 and a.shape[1] == 2
+    return a
+
+
+@dataclass
+class Result:
+    status: int
+    points: int
+    n_tiles: int          # D: distinct tiles
+    n_significant: int    # S: tiles with count >= tau
+    n_clusters: int
+    key: np.ndarray       # kept tiles, (ix, iy) order
+    count: np.ndarray
+    cid: np.ndarray
+
+
+class Oracle:
+    """Chunked oracle session: add() per chunk, then finish()."""
+
+    def __init__(self, precision: float, tau: int, mu: int, scale: float | None = None, lib=None):
+        self.L = lib if lib is not None else _load()
+        self.scale = scale_of(precision) if scale is None else scale
+        self.h = self.L.oracle_create(self.scale, tau, mu)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.L.oracle_free(self.h)
+            self.h = None
+
+    def add(self, xy) -> int:
+        a = _xy(xy)
+        return self.L.oracle_add(self.h, a.ctypes.data, a.shape[0])
+
+    def finish(self) -> Result:
+        st = self.L.oracle_finish(self.h)
+        k = self.L.oracle_n_kept(self.h)
+        key = np.empty(k, np.int64)
+        cnt = np.empty(k, np.uint64)
+        cid = np.empty(k, np.int64)
+        self.L.oracle_copy_kept(self.h, key.ctypes.data, cnt.ctypes.data, cid.ctypes.data)
+        return Result(status=st, points=self.L.oracle_points(self.h), n_tiles=self.L.oracle_n_tiles(self.h),
+                      n_significant=self.L.oracle_n_significant(self.h),
+                      n_clusters=self.L.oracle_n_clusters(self.h), key=key, count=cnt, cid=cid)
+
+    def tiles(self) -> tuple[np.ndarray, np.ndarray]:
+        d = self.L.oracle_n_tiles(self.h)
+        key = np.empty(d, np.int64)
+        cnt = np.empty(d, np.uint64)
+        self.L.oracle_copy_tiles(self.h, key.ctypes.data, cnt.ctypes.data)
+        return key, cnt
+
+    def labels(self, xy) -> tuple[int, np.ndarray]:
+        a = _xy(xy)
+        out = np.empty(a.shape[0], np.int64)
+        st = self.L.oracle_labels(self.h, a.ctypes.data, a.shape[0], out.ctypes.data)
+        return st, out
+
+
+def raster(xy, precision: float, tau: int, mu: int, scale: float | None = None, chunks: int = 1,
+           with_labels: bool = False, lib=None):
+    """Run the oracle on one point set; optionally in ``chunks`` contiguous chunks."""
+    o = Oracle(precision, tau, mu, scale, lib=lib)
+    a = _xy(xy)
+    n = a.shape[0]
+    for c in range(chunks):
+        o.add(a[n * c // chunks: n * (c + 1) // chunks])
+    r = o.finish()
+    if with_labels:
+        st, lab = o.labels(a)
+        return r, lab, o
+    return r, o
+
+
+def project(xy, scale: float) -> tuple[np.ndarray, np.ndarray]:
+    a = _xy(xy)
+    keys = np.empty(a.shape[0], np.int64)
+    ok = np.empty(a.shape[0], np.uint8)
+    _load().oracle_project(a.ctypes.data, a.shape[0], scale, keys.ctypes.data, ok.ctypes.data)
+    return keys, ok.astype(bool)
+
+
+def count_keys(xy, scale: float, keys) -> np.ndarray:
+    a = _xy(xy)
+    k = np.ascontiguousarray(keys, dtype=np.int64)
+    out = np.empty(k.shape[0], np.uint64)
+    _load().oracle_count_keys(a.ctypes.data, a.shape[0], scale, k.ctypes.data, k.shape[0], out.ctypes.data)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Key helpers (plain definitions of the packing convention).
+def pack(ix, iy):
+    ix = np.asarray(ix, dtype=np.int64)
+    iy = np.asarray(iy, dtype=np.int64)
+    return ((ix << 32) | (iy & 0xFFFFFFFF)).astype(np.int64)
+
+
+def unpack(key):
+    key = np.asarray(key, dtype=np.int64)
+    return (key >> 32).astype(np.int64), (key & 0xFFFFFFFF).astype(np.uint32).astype(np.int32).astype(np.int64)
+
+
+def tile_order(key) -> np.ndarray:
+    """Indices that sort keys in (ix, iy) lexicographic order."""
+    ix, iy = unpack(key)
+    return np.lexsort((iy, ix))
+
+
+# ---------------------------------------------------------------------------
+# Independent restatements used only to pin the oracle on small inputs.
+def project_exact(x: float, scale: float):
+    """floor(RN(x * s)) by exact rational arithmetic: the product of the two
+    binary64 values is formed exactly, rounded once to the nearest double
+    (ties to even, which is what float(Fraction) does), then floored.
+    Returns None when the result is not a valid tile index."""
+    import math
+    if not (math.isfinite(x) and math.isfinite(scale)):
+        return None
+    exact = Fraction(x) * Fraction(scale)
+    try:
+        q = float(exact)  # correctly rounded
+    except OverflowError:
+        return None
+    if not math.isfinite(q):
+        return None
+    f = math.floor(q)
+    if f < -(2**31 - 1) or f > 2**31 - 2:
+        return None
+    return f
+
+
+def brute_force(keys, counts, tau: int, mu: int):
+    """RASTER agglomeration by all-pairs adjacency: tiles with count >= tau are
+    joined when max(|dx|, |dy|) == 1, via union-find; components with at least
+    mu tiles are kept; the id is the (ix, iy)-smallest member.  O(T^2); tiny T."""
+    keys = np.asarray(keys, dtype=np.int64)
+    counts = np.asarray(counts)
+    sig = keys[counts >= tau]
+    ix, iy = unpack(sig)
+    t = len(sig)
+    parent = list(range(t))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for a in range(t):
+        for b in range(a + 1, t):
+            if max(abs(int(ix[a]) - int(ix[b])), abs(int(iy[a]) - int(iy[b]))) == 1:
+                ra, rb = find(a), find(b)
+                if ra != rb:
+                    parent[rb] = ra
+    comps: dict[int, list[int]] = {}
+    for a in range(t):
+        comps.setdefault(find(a), []).append(a)
+    rows = []
+    n_clusters = 0
+    for members in comps.values():
+        if len(members) < mu:
+            continue
+        n_clusters += 1
+        best = min(members, key=lambda m: (int(ix[m]), int(iy[m])))
+        for m in members:
+            rows.append((int(sig[m]), int(sig[best])))
+    rows.sort(key=lambda r: (r[0] >> 32, np.int32(np.uint32(r[0] & 0xFFFFFFFF))))
+    cnt_of = {int(k): int(c) for k, c in zip(keys, counts)}
+    key = np.array([r[0] for r in rows], dtype=np.int64)
+    cid = np.array([r[1] for r in rows], dtype=np.int64)
+    cnt = np.array([cnt_of[int(k)] for k in key], dtype=np.uint64)
+    return key, cnt, cid, n_clusters

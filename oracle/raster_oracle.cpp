@@ -1,0 +1,281 @@
+/*
+ * RASTER oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU statement of what the RASTER hot path
+ * computes, used to check the CUDA library.  Only the tests, the package's
+ * smoke check and the benchmark's CPU-baseline leg may load it; the library
+ * never does.  It shares no code, header or table with the CUDA path.
+ *
+ * It follows Alg. 1 (RASTER) of Ulm et al., "Contraction Clustering (RASTER)":
+ *   contraction   -- project every point to its tile and count points per
+ *                    tile (Alg. 1, first loop; Sect. 3.2), then drop tiles
+ *                    with fewer than tau points (Alg. 1, second loop);
+ *   agglomeration -- repeatedly pop a significant tile and collect every
+ *                    significant tile reachable through neighbours at
+ *                    Chebyshev distance 1 (Alg. 1, while loop; Sect. 3.2,
+ *                    "eight neighbors"), keeping clusters of at least mu tiles.
+ * Points may arrive in any number of chunks ("Working with huge data sets",
+ * Sect. 3.6); the counts only depend on the multiset of points.
+ *
+ * Readings where the paper leaves a choice open (each is a fixed convention
+ * of this project, shared with the CUDA library by specification only):
+ *   - projection: ix = floor(fl(x * s)) with s = 10^precision held as one
+ *     double, fl() one IEEE-754 binary64 multiply rounded to nearest even
+ *     (build with -ffp-contract=off so no fused multiply-add appears);
+ *     floor, not truncation toward zero, so tiles are uniform across 0;
+ *   - a tile index must lie in [INT32_MIN+1, INT32_MAX-1]; a non-finite or
+ *     out-of-range coordinate is an error (ORACLE_RANGE) and that point is
+ *     skipped;
+ *   - key = (int64)ix << 32 | (uint32)iy;
+ *   - significant: count >= tau; kept: cluster size (in tiles) >= mu;
+ *   - cluster id = key of the cluster's smallest tile in (ix, iy)
+ *     lexicographic order; noise label = INT64_MIN;
+ *   - outputs are listed in (ix, iy) lexicographic order.
+ */
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+namespace {
+
+const int ORACLE_OK = 0;
+const int ORACLE_RANGE = 2;
+const int64_t NOISE = INT64_MIN;
+
+struct Tile {
+    int32_t ix, iy;
+};
+
+int64_t pack(int32_t ix, int32_t iy) {
+    return (int64_t)(((uint64_t)(uint32_t)ix << 32) | (uint64_t)(uint32_t)iy);
+}
+int32_t tile_x(int64_t key) { return (int32_t)(uint32_t)((uint64_t)key >> 32); }
+int32_t tile_y(int64_t key) { return (int32_t)(uint32_t)((uint64_t)key & 0xffffffffu); }
+
+/* (ix, iy) lexicographic order on keys. */
+bool tile_less(int64_t a, int64_t b) {
+    if (tile_x(a) != tile_x(b)) return tile_x(a) < tile_x(b);
+    return tile_y(a) < tile_y(b);
+}
+
+/* project(x, y, prec) of Alg. 1: one coordinate.  Returns false when the
+ * scaled coordinate is not finite or its floor leaves the valid range. */
+bool project_coord(double v, double scale, int32_t *out) {
+    volatile double scaled = v * scale;  /* one rounded multiply */
+    double f = std::floor(scaled);
+    if (!(f >= -2147483647.0 && f <= 2147483646.0)) return false;  /* also rejects NaN */
+    *out = (int32_t)f;
+    return true;
+}
+
+bool project(double x, double y, double scale, int64_t *key) {
+    int32_t ix, iy;
+    if (!project_coord(x, scale, &ix) || !project_coord(y, scale, &iy)) return false;
+    *key = pack(ix, iy);
+    return true;
+}
+
+}  // namespace
+
+struct oracle_state {
+    double scale;
+    uint32_t tau, mu;
+    int status;
+    int64_t points;
+    /* acc of Alg. 1: tile -> number of points */
+    std::unordered_map<int64_t, uint64_t> acc;
+    /* agglomeration results */
+    bool finished;
+    int64_t n_significant;
+    std::vector<int64_t> kept_key;
+    std::vector<uint64_t> kept_count;
+    std::vector<int64_t> kept_cid;
+    int64_t n_clusters;
+    std::unordered_map<int64_t, int64_t> cid_of;  /* kept tile -> cluster id */
+};
+
+extern "C" {
+
+oracle_state *oracle_create(double scale, uint32_t tau, uint32_t mu) {
+    oracle_state *s = new oracle_state();
+    s->scale = scale;
+    s->tau = tau;
+    s->mu = mu;
+    s->status = ORACLE_OK;
+    s->points = 0;
+    s->finished = false;
+    s->n_significant = 0;
+    s->n_clusters = 0;
+    return s;
+}
+
+void oracle_free(oracle_state *s) { delete s; }
+
+/* Contraction for one chunk of points (Alg. 1, first loop). */
+int oracle_add(oracle_state *s, const double *xy, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t key;
+        if (!project(xy[2 * i], xy[2 * i + 1], s->scale, &key)) {
+            s->status = ORACLE_RANGE;
+            continue;
+        }
+        auto it = s->acc.find(key);
+        if (it == s->acc.end())
+            s->acc[key] = 1;
+        else
+            it->second += 1;
+        s->points += 1;
+    }
+    s->finished = false;
+    return s->status;
+}
+
+/* Threshold and agglomeration (Alg. 1, second loop and while loop). */
+int oracle_finish(oracle_state *s) {
+    /* second loop: keep the tiles with at least tau points */
+    std::unordered_set<int64_t> sigma;
+    for (const auto &kv : s->acc)
+        if (kv.second >= s->tau) sigma.insert(kv.first);
+    s->n_significant = (int64_t)sigma.size();
+
+    s->kept_key.clear();
+    s->kept_count.clear();
+    s->kept_cid.clear();
+    s->cid_of.clear();
+    s->n_clusters = 0;
+
+    /* while loop: pop a tile, gather its cluster by visiting neighbours */
+    std::vector<std::vector<int64_t>> clusters;
+    while (!sigma.empty()) {
+        int64_t t = *sigma.begin();
+        sigma.erase(sigma.begin());
+        std::vector<int64_t> cluster;
+        std::deque<int64_t> visit;
+        visit.push_back(t);
+        while (!visit.empty()) {
+            int64_t u = visit.front();
+            visit.pop_front();
+            int32_t ux = tile_x(u), uy = tile_y(u);
+            std::vector<int64_t> ns;
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy) {
+                    if (dx == 0 && dy == 0) continue;
+                    int64_t nx = (int64_t)ux + dx, ny = (int64_t)uy + dy;
+                    /* tiles outside the valid index range never exist */
+                    if (nx < -2147483647LL || nx > 2147483646LL) continue;
+                    if (ny < -2147483647LL || ny > 2147483646LL) continue;
+                    int64_t nk = pack((int32_t)nx, (int32_t)ny);
+                    if (sigma.count(nk)) ns.push_back(nk);
+                }
+            cluster.push_back(u);
+            for (int64_t k : ns) {
+                sigma.erase(k);
+                visit.push_back(k);
+            }
+        }
+        if (cluster.size() >= s->mu) clusters.push_back(cluster);
+    }
+
+    /* emit kept tiles with their cluster id = smallest tile of the cluster */
+    std::vector<std::pair<int64_t, int64_t>> rows;  /* (key, cid) */
+    for (const auto &c : clusters) {
+        int64_t cid = c[0];
+        for (int64_t k : c)
+            if (tile_less(k, cid)) cid = k;
+        for (int64_t k : c) rows.push_back({k, cid});
+        s->cid_of.reserve(s->cid_of.size() + c.size());
+        for (int64_t k : c) s->cid_of[k] = cid;
+    }
+    std::sort(rows.begin(), rows.end(),
+              [](const std::pair<int64_t, int64_t> &a, const std::pair<int64_t, int64_t> &b) {
+                  return tile_less(a.first, b.first);
+              });
+    for (const auto &r : rows) {
+        s->kept_key.push_back(r.first);
+        s->kept_count.push_back(s->acc[r.first]);
+        s->kept_cid.push_back(r.second);
+    }
+    s->n_clusters = (int64_t)clusters.size();
+    s->finished = true;
+    return s->status;
+}
+
+int oracle_status(const oracle_state *s) { return s->status; }
+int64_t oracle_points(const oracle_state *s) { return s->points; }
+int64_t oracle_n_tiles(const oracle_state *s) { return (int64_t)s->acc.size(); }
+int64_t oracle_n_significant(const oracle_state *s) { return s->n_significant; }
+int64_t oracle_n_kept(const oracle_state *s) { return (int64_t)s->kept_key.size(); }
+int64_t oracle_n_clusters(const oracle_state *s) { return s->n_clusters; }
+
+/* All tiles with their counts, in (ix, iy) order. */
+void oracle_copy_tiles(const oracle_state *s, int64_t *key, uint64_t *count) {
+    std::vector<int64_t> keys;
+    keys.reserve(s->acc.size());
+    for (const auto &kv : s->acc) keys.push_back(kv.first);
+    std::sort(keys.begin(), keys.end(), tile_less);
+    for (size_t i = 0; i < keys.size(); ++i) {
+        key[i] = keys[i];
+        count[i] = s->acc.at(keys[i]);
+    }
+}
+
+/* Tiles of kept clusters with (count, cluster id), in (ix, iy) order. */
+void oracle_copy_kept(const oracle_state *s, int64_t *key, uint64_t *count, int64_t *cid) {
+    for (size_t i = 0; i < s->kept_key.size(); ++i) {
+        key[i] = s->kept_key[i];
+        count[i] = s->kept_count[i];
+        cid[i] = s->kept_cid[i];
+    }
+}
+
+/* Per-point labels: the RASTER* second pass (Sect. 4.1, Experiment 1) that
+ * projects every point again and reports its tile's cluster, or noise.
+ * Returns ORACLE_RANGE if some point could not be projected (it gets noise). */
+int oracle_labels(const oracle_state *s, const double *xy, int64_t n, int64_t *labels) {
+    int st = ORACLE_OK;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t key;
+        if (!project(xy[2 * i], xy[2 * i + 1], s->scale, &key)) {
+            labels[i] = NOISE;
+            st = ORACLE_RANGE;
+            continue;
+        }
+        auto it = s->cid_of.find(key);
+        labels[i] = (it == s->cid_of.end()) ? NOISE : it->second;
+    }
+    return st;
+}
+
+/* Projection alone, for pinning: keys[i] and ok[i] (1 valid, 0 range error). */
+void oracle_project(const double *xy, int64_t n, double scale, int64_t *keys, uint8_t *ok) {
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t key = 0;
+        bool good = project(xy[2 * i], xy[2 * i + 1], scale, &key);
+        keys[i] = good ? key : 0;
+        ok[i] = good ? 1 : 0;
+    }
+}
+
+/* Exact counts of a given set of tiles over a point set (one pass), used to
+ * check sampled outputs of very large runs one by one. */
+void oracle_count_keys(const double *xy, int64_t n, double scale, const int64_t *keys, int64_t k,
+                       uint64_t *counts) {
+    std::unordered_map<int64_t, int64_t> where;
+    for (int64_t j = 0; j < k; ++j) {
+        where[keys[j]] = j;
+        counts[j] = 0;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t key;
+        if (!project(xy[2 * i], xy[2 * i + 1], scale, &key)) continue;
+        auto it = where.find(key);
+        if (it != where.end()) counts[it->second] += 1;
+    }
+}
+
+}  // extern "C"

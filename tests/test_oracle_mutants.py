@@ -1,0 +1,93 @@
+"""Planted mistakes: each test compiles a copy of the oracle with one
+deliberate error (a dropped term, a wrong comparison, a transposed operand...)
+and checks that the oracle's pins reject it.  CPU only."""
+import os
+import random
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "raster_oracle.cpp")
+
+MUTANTS = {
+    "four_connected": ("if (dx == 0 && dy == 0) continue;",
+                       "if (dx == 0 && dy == 0) continue;\n if (dx != 0 && dy != 0) continue;"),
+    "strict_tau": ("kv.second >= s->tau", "kv.second > s->tau"),
+    "truncate_not_floor": ("std::floor(scaled)", "std::trunc(scaled)"),
+    "strict_mu": ("cluster.size() >= s->mu", "cluster.size() > s->mu"),
+    "max_id": ("if (tile_less(k, cid)) cid = k;", "if (tile_less(cid, k)) cid = k;"),
+    "transposed_key": ("*key = pack(ix, iy);", "*key = pack(iy, ix);"),
+    "single_precision_scale": ("v * scale", "v * (double)(float)scale"),
+    "lost_increment": ("it->second += 1;", "it->second += (it->second > 3) ? 0 : 1;"),
+    "range_off_by_one": ("f <= 2147483646.0", "f <= 2147483647.0"),
+}
+
+
+def _pins_pass(lib) -> bool:
+    """A compact run of the oracle pins; False as soon as one disagrees."""
+    # Sect. 3.2 worked example
+    pts = np.array([[1.005, 1.000], [1.009, 1.002], [1.008, 1.006]])
+    r, o = oracle.raster(pts, 2, 3, 1, lib=lib)
+    k, c = o.tiles()
+    if list(k) != [oracle.pack(100, 100)] or list(c) != [3] or r.n_significant != 1:
+        return False
+    # exact rounding of the product, incl. negatives and range limits
+    rng = random.Random(5)
+    xs = [rng.uniform(-30, 30) for _ in range(300)] + [-0.005, 0.29, 21474836.46, 21474836.47,
+                                                       -21474836.47, 1.0 + 2 ** -40]
+    xy = np.array([xs, xs[::-1]]).T.copy()
+    for p in (2, 3.5, 0.73):
+        s = oracle.scale_of(p)
+        o = oracle.Oracle(p, 1, 1, lib=lib)
+        o.add(xy)
+        keys, _ = o.tiles()
+        expect = set()
+        for x, y in xy:
+            ex, ey = oracle.project_exact(x, s), oracle.project_exact(y, s)
+            if ex is not None and ey is not None:
+                expect.add(int(oracle.pack(ex, ey)))
+        if set(keys.tolist()) != expect:
+            return False
+    # counts vs numpy, and all-pairs agglomeration
+    for seed in range(6):
+        rng = random.Random(seed)
+        tiles = []
+        for _ in range(40):
+            x0, y0 = rng.randint(-15, 15), rng.randint(-15, 15)
+            for _ in range(rng.randint(1, 6)):
+                tiles.append((x0 + rng.randint(-1, 1), y0 + rng.randint(-1, 1)))
+        xy = []
+        for (a, b) in tiles:
+            for _ in range(rng.randint(1, 9)):
+                xy.append(((a + rng.uniform(0.05, 0.95)) / 100.0, (b + rng.uniform(0.05, 0.95)) / 100.0))
+        xy = np.array(xy)
+        tau, mu = rng.choice([2, 3, 5]), rng.choice([2, 3, 4])
+        r, o = oracle.raster(xy, 2, tau, mu, lib=lib)
+        keys, counts = o.tiles()
+        f = np.floor(xy * 100.0).astype(np.int64)
+        uk, uc = np.unique(oracle.pack(f[:, 0], f[:, 1]), return_counts=True)
+        if sorted(zip(keys.tolist(), counts.tolist())) != sorted(zip(uk.tolist(), uc.tolist())):
+            return False
+        bk, bc, bcid, bn = oracle.brute_force(uk, uc, tau, mu)
+        if not (np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and r.n_clusters == bn
+                and np.array_equal(r.count, bc)):
+            return False
+    return True
+
+
+def test_real_oracle_passes_compact_pins():
+    assert _pins_pass(None)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mutated = tmp_path / f"oracle_{name}.cpp"
+    mutated.write_text(src.replace(old, new))
+    lib = oracle.load_library(oracle.compile_source(str(mutated), str(tmp_path / f"lib_{name}.so")))
+    assert not _pins_pass(lib), f"mutant {name} slipped through the pins"
