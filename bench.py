@@ -1,0 +1,328 @@
+"""RASTER benchmark: points/s of the whole hot path on one GB300 (or N replicas).
+
+A step is one pass of the plain RASTER hot path over the 500M-point workload
+(1,000,000 square clusters of 475 points in [0, 3000)^2 plus 25M uniform
+noise points, shuffled; precision 2, tau 5, mu 4):
+    reset -> contract (projection + tile counting) -> agglomerate (tau filter,
+    8-connected components, mu filter, cluster ids) -> per-point labels.
+
+value : points/s with the points already resident in HBM (CUDA events).
+e2e   : the same step through the host-buffer entry points (pinned host
+        points in, labels out), copies inside the timed region.
+roofline : the contraction phase, algorithmic bytes (16 B per point read +
+        12 B per distinct tile written) over its measured time, against the
+        measured HBM copy bandwidth.
+cpu_baseline : the CPU oracle on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+       (N > 1 under torch.distributed.run: one independent replica per GPU.)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gen  # noqa: E402
+
+TILE_BYTES = 12          # algorithmic bytes per distinct tile (key + count written once)
+POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="500m", choices=sorted(gen.NAMED))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="points of the oracle sample")
+    ap.add_argument("--profile", action="store_true", help="short run for ncu (no clocks/e2e/cpu legs)")
+    ap.add_argument("--points", type=int, default=0, help="use only the first N points (profiling cases)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(w: gen.Workload, name: str) -> dict:
+    return {"workload": f"raster-{name}", "n_points": w.n, "clusters": w.clusters,
+            "cluster_points": w.cluster_points, "canvas": [0.0, w.canvas], "precision": w.precision,
+            "tau": w.tau, "mu": w.mu, "point_dtype": "float64x2", "order": "shuffled", "seed": w.seed,
+            "l2": "inputs (16 B/point) far larger than L2; no flush needed"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        hi = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(hi), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the reference arm and the cpu_baseline leg)
+
+def oracle_sample(w: gen.Workload, sample: int):
+    """Time the oracle (contraction, agglomeration, labels) on the first
+    `sample` points of the workload; returns points/s and a description."""
+    import oracle
+    xy = gen.points(w, 0, min(sample, w.n))
+    t0 = time.perf_counter()
+    o = oracle.Oracle(w.precision, w.tau, w.mu)
+    o.add(xy)
+    o.finish()
+    o.labels(xy)
+    dt = time.perf_counter() - t0
+    return xy.shape[0] / dt, dt, f"first {xy.shape[0]:,} points of the workload (contract + agglomerate + labels)"
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    w = gen.NAMED[args.workload]
+    if rank != 0:
+        return
+    times = []
+    sample = max(1, args.cpu_sample // 5)
+    for i in range(args.warmup + args.steps):
+        rate, dt, desc = oracle_sample(w, sample)
+        if i >= args.warmup:
+            times.append(dt)
+    v = sample / statistics.mean(times)
+    line = {"impl": "reference", "metric": "points_per_s", "value": v, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, args.workload),
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {sample:,} points of the workload per step"},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1907_03620_gb300 as R
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = gen.NAMED[args.workload]
+    if args.points:  # same density, fewer points: scale clusters and canvas area
+        f = args.points / w.n
+        w = gen.Workload(**dict(w.asdict(), n=args.points, clusters=max(1, round(w.clusters * f)),
+                                cluster_points=round(w.cluster_points * f), canvas=w.canvas * f ** 0.5))
+    L = R.lib()
+
+    # inputs: pinned host copy (for e2e) and a device-resident copy
+    host = torch.empty((w.n, 2), dtype=torch.float64, pin_memory=True)
+    gen.points_into(host.numpy(), w)
+    xy = host.to(dev, non_blocking=False)
+    labels = torch.empty(w.n, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    r = R.Raster(w.precision, w.tau, w.mu)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(record=None):
+        e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
+        e0.record(stream)
+        r.reset()
+        e1.record(stream)
+        r.contract(xy)
+        e2.record(stream)
+        res = r.agglomerate(copy=False)
+        e3.record(stream)
+        r.point_labels(xy, out=labels)
+        e4.record(stream)
+        if record is not None:
+            record.append((e0, e1, e2, e3, e4, res))
+        return res
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if not args.profile:
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = L.raster_kernel_launches()
+    recs = []
+    t_start, t_end = ev(), ev()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(recs)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = L.raster_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if not args.profile else None
+
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    phase = {"reset": [], "contract": [], "agglomerate": [], "labels": []}
+    for (e0, e1, e2, e3, e4, res) in recs:
+        phase["reset"].append(e0.elapsed_time(e1))
+        phase["contract"].append(e1.elapsed_time(e2))
+        phase["agglomerate"].append(e2.elapsed_time(e3))
+        phase["labels"].append(e3.elapsed_time(e4))
+    res = recs[-1][5]
+    ms_step = total_ms / args.steps
+    value = world * w.n / (ms_step / 1e3)
+
+    peaks = measured_peaks()
+    contract_ms = statistics.mean(phase["contract"])
+    alg_bytes = POINT_BYTES * w.n + TILE_BYTES * res.n_distinct
+    achieved = alg_bytes / (contract_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_contract (contraction phase)", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": peaks["source"], "traffic": None,
+                "algorithmic_bytes": alg_bytes, "phase_ms": contract_ms}
+
+    line = {"metric": "points_per_s", "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}"),
+            "phases_ms": {k: statistics.mean(v) for k, v in phase.items()},
+            "stats": {"n_distinct": res.n_distinct, "n_significant": res.n_significant,
+                      "n_clusters": res.n_clusters, "kept_tiles": int(res.key.numel()),
+                      "table_slots": r.capacity},
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+
+    # e2e: host buffers through the C ABI, copies inside the timed region
+    if not args.no_e2e and not args.profile:
+        lab_host = torch.empty(w.n, dtype=torch.int64, pin_memory=True)
+
+        def e2e_step():
+            r.reset()
+            r.contract_host(host)
+            res = r.agglomerate(copy=False)
+            r.point_labels_host(host, out=lab_host)
+            return res
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": world * w.n / dt, "unit": "points/s", "h2d_bytes_per_step": POINT_BYTES * w.n,
+                       "d2h_bytes_per_step": 8 * w.n, "ms_per_step": dt * 1e3, "steps": n_e2e}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile:
+        rate, dt, desc = oracle_sample(w, args.cpu_sample)
+        line["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+
+    r.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

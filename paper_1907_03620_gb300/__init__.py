@@ -1,0 +1,209 @@
+"""GB300-native RASTER (contraction clustering) -- Python binding.
+
+Thin wrapper over the C ABI in ``include/raster.h`` (libraster.so): argument
+marshalling only; every step of the clustering runs in the CUDA kernels.
+PyTorch supplies device memory and streams.
+
+    r = Raster(precision=2, tau=5, mu=4)
+    r.contract(xy_cuda)            # (n, 2) float64 CUDA tensor; callable per chunk
+    res = r.agglomerate()          # kept tiles: key, count, cid (CUDA tensors)
+    labels = r.point_labels(xy_cuda)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _native
+from ._native import NOISE, RasterError, check, lib
+
+__all__ = ["Raster", "Result", "RasterError", "NOISE", "lib", "build", "pack", "unpack"]
+
+
+def build(force: bool = False) -> str:
+    from . import builder as _b
+    return _b.build(force=force)
+
+
+def pack(ix: torch.Tensor, iy: torch.Tensor) -> torch.Tensor:
+    return (ix.to(torch.int64) << 32) | (iy.to(torch.int64) & 0xFFFFFFFF)
+
+
+def unpack(key: torch.Tensor):
+    return key >> 32, (key & 0xFFFFFFFF).to(torch.int32).to(torch.int64)
+
+
+class _DeviceArray:
+    """Wraps a device pointer owned by the library for torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, device: torch.device):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False),
+                                         "version": 3, "strides": None}
+        self.device = device
+
+
+def _view(ptr: int, n: int, dtype: torch.dtype, device: torch.device) -> torch.Tensor:
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=device)
+    typestr = {torch.int64: "<i8", torch.int32: "<i4"}[dtype]
+    return torch.as_tensor(_DeviceArray(ptr, n, typestr, device), device=device)
+
+
+@dataclass
+class Result:
+    """Tiles of kept clusters (one row per tile) and run statistics."""
+    key: torch.Tensor     # int64 packed tile keys
+    count: torch.Tensor   # int64 points per tile
+    cid: torch.Tensor     # int64 cluster id (key of the cluster's (ix, iy)-smallest tile)
+    n_clusters: int
+    n_distinct: int
+    n_significant: int
+    n_points: int
+    status: int
+
+    def sorted(self) -> "Result":
+        """Rows in (ix, iy) order (the library's row order is unspecified)."""
+        if self.key.numel() == 0:
+            return self
+        ix, iy = unpack(self.key)
+        order = torch.argsort(iy, stable=True)
+        order = order[torch.argsort(ix[order], stable=True)]
+        return Result(self.key[order], self.count[order], self.cid[order], self.n_clusters, self.n_distinct,
+                      self.n_significant, self.n_points, self.status)
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_points(xy: torch.Tensor, where: str):
+    if not (xy.is_cuda and xy.dtype == torch.float64 and xy.dim() == 2 and xy.shape[1] == 2 and xy.is_contiguous()):
+        raise ValueError(f"{where}: expected a contiguous (n, 2) float64 CUDA tensor")
+
+
+class Raster:
+    """One RASTER problem (precision, tau, mu) with a device-resident tile table."""
+
+    def __init__(self, precision: float, tau: int, mu: int):
+        self._L = lib()
+        h = ctypes.c_void_p()
+        check(self._L.raster_create(float(precision), int(tau), int(mu), ctypes.byref(h)), "raster_create")
+        self._h = h
+        self.precision, self.tau, self.mu = precision, tau, mu
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.raster_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def scale(self) -> float:
+        return self._L.raster_get_scale(self._h)
+
+    @property
+    def capacity(self) -> int:
+        return self._L.raster_table_capacity(self._h)
+
+    # -- hot path ------------------------------------------------------------
+    def reserve(self, n_tiles: int):
+        check(self._L.raster_reserve(self._h, int(n_tiles)), "raster_reserve")
+
+    def contract(self, xy: torch.Tensor, stream=None):
+        _check_points(xy, "contract")
+        check(self._L.raster_contract(self._h, ctypes.c_void_p(xy.data_ptr()), xy.shape[0], _stream_ptr(stream)),
+              "raster_contract")
+
+    def contract_host(self, xy, stream=None):
+        """xy: host (n, 2) float64 (pinned torch tensor or numpy array)."""
+        ptr, n = _host_ptr(xy)
+        check(self._L.raster_contract_host(self._h, ctypes.c_void_p(ptr), n, _stream_ptr(stream)),
+              "raster_contract_host")
+
+    def agglomerate(self, copy: bool = True, allow_range_error: bool = False) -> Result:
+        out = _native.Clusters()
+        st = self._L.raster_agglomerate(self._h, ctypes.byref(out))
+        if st != _native.OK and not (allow_range_error and st == _native.E_RANGE):
+            raise RasterError(st, "raster_agglomerate")
+        n = out.n_tiles
+        key = _view(out.key, n, torch.int64, self.device)
+        cnt = _view(out.count, n, torch.int32, self.device)
+        cid = _view(out.cid, n, torch.int64, self.device)
+        if copy:
+            key, cid = key.clone(), cid.clone()
+        cnt = cnt.to(torch.int64) & 0xFFFFFFFF
+        return Result(key, cnt, cid, out.n_clusters, out.n_distinct, out.n_significant, out.n_points, st)
+
+    def point_labels(self, xy: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        _check_points(xy, "point_labels")
+        if out is None:
+            out = torch.empty(xy.shape[0], dtype=torch.int64, device=xy.device)
+        assert out.is_cuda and out.dtype == torch.int64 and out.is_contiguous() and out.numel() == xy.shape[0]
+        check(self._L.raster_point_labels(self._h, ctypes.c_void_p(xy.data_ptr()), xy.shape[0],
+                                          ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+              "raster_point_labels")
+        return out
+
+    def point_labels_host(self, xy, out=None, stream=None):
+        ptr, n = _host_ptr(xy)
+        if out is None:
+            out = torch.empty(n, dtype=torch.int64)
+        optr, on = _host_ptr(out, cols=None)
+        assert on == n
+        check(self._L.raster_point_labels_host(self._h, ctypes.c_void_p(ptr), n, ctypes.c_void_p(optr),
+                                               _stream_ptr(stream)), "raster_point_labels_host")
+        return out
+
+    def export_tiles(self):
+        """All tiles with at least one point: (key int64, count int64) CUDA tensors."""
+        n = ctypes.c_int64()
+        self._L.raster_export_tiles(self._h, None, None, 0, ctypes.byref(n))
+        d = n.value
+        key = torch.empty(max(d, 1), dtype=torch.int64, device=self.device)
+        cnt = torch.empty(max(d, 1), dtype=torch.int32, device=self.device)
+        check(self._L.raster_export_tiles(self._h, ctypes.c_void_p(key.data_ptr()), ctypes.c_void_p(cnt.data_ptr()),
+                                          max(d, 1), ctypes.byref(n)), "raster_export_tiles")
+        return key[:d], cnt[:d].to(torch.int64) & 0xFFFFFFFF
+
+    def reset(self, stream=None):
+        check(self._L.raster_reset(self._h, _stream_ptr(stream)), "raster_reset")
+
+    def status(self) -> int:
+        return self._L.raster_status(self._h)
+
+
+def _host_ptr(a, cols=2):
+    import numpy as np
+    if isinstance(a, np.ndarray):
+        if cols is None:
+            assert a.dtype == np.int64 and a.flags.c_contiguous and a.ndim == 1
+            return a.ctypes.data, a.shape[0]
+        assert a.dtype == np.float64 and a.flags.c_contiguous and a.ndim == 2 and a.shape[1] == cols
+        return a.ctypes.data, a.shape[0]
+    assert not a.is_cuda and a.is_contiguous()
+    if cols is None:
+        assert a.dtype == torch.int64 and a.dim() == 1
+    else:
+        assert a.dtype == torch.float64 and a.dim() == 2 and a.shape[1] == cols
+    return a.data_ptr(), a.shape[0]

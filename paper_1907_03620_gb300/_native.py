@@ -1,0 +1,93 @@
+"""ctypes loader for libraster.so: argument marshalling only.
+
+The library is built in-tree by ``paper_1907_03620_gb300.build``.  There is no
+CPU fallback: if the shared library is missing or fails to load, every entry
+point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+from . import builder as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+E_ARG, E_RANGE, E_OOM, E_TABLE_FULL, E_CUDA, E_INTERNAL, E_STATE = 1, 2, 3, 4, 5, 6, 7
+NOISE = -(2 ** 63)
+NAMES = {0: "RASTER_OK", 1: "RASTER_E_ARG", 2: "RASTER_E_RANGE", 3: "RASTER_E_OOM", 4: "RASTER_E_TABLE_FULL",
+         5: "RASTER_E_CUDA", 6: "RASTER_E_INTERNAL", 7: "RASTER_E_STATE"}
+
+
+class RasterError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().raster_strerror(status).decode() if _lib is not None else ""
+        super().__init__(f"{where}: {NAMES.get(status, status)} ({msg})")
+
+
+class Clusters(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_void_p), ("count", ctypes.c_void_p), ("cid", ctypes.c_void_p),
+                ("n_tiles", ctypes.c_int64), ("n_clusters", ctypes.c_int64), ("n_distinct", ctypes.c_int64),
+                ("n_significant", ctypes.c_int64), ("n_points", ctypes.c_int64)]
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/*.h (for export checks)."""
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    names = []
+    for fn in sorted(os.listdir(inc)):
+        if fn.endswith(".h"):
+            src = open(os.path.join(inc, fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(raster_[a-z0-9_]+)\s*\(",
+                                src, flags=re.M)
+    return sorted(set(names))
+
+
+def _declare(L):
+    vp, i64, u32, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_int
+    sig = {
+        "raster_create": (ci, [dbl, u32, u32, ctypes.POINTER(vp)]),
+        "raster_reserve": (ci, [vp, i64]),
+        "raster_contract": (ci, [vp, vp, i64, vp]),
+        "raster_contract_host": (ci, [vp, vp, i64, vp]),
+        "raster_agglomerate": (ci, [vp, ctypes.POINTER(Clusters)]),
+        "raster_point_labels": (ci, [vp, vp, i64, vp, vp]),
+        "raster_point_labels_host": (ci, [vp, vp, i64, vp, vp]),
+        "raster_export_tiles": (ci, [vp, vp, vp, i64, ctypes.POINTER(i64)]),
+        "raster_reset": (ci, [vp, vp]),
+        "raster_status": (ci, [vp]),
+        "raster_get_scale": (dbl, [vp]),
+        "raster_table_capacity": (i64, [vp]),
+        "raster_destroy": (ci, [vp]),
+        "raster_kernel_launches": (ctypes.c_uint64, []),
+        "raster_strerror": (ctypes.c_char_p, [ci]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def lib():
+    """Load (building first if needed) the native library; raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
+            L = ctypes.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def check(status: int, where: str):
+    if status != OK:
+        raise RasterError(status, where)
