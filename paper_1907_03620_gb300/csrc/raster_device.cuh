@@ -20,6 +20,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "raster_project.cuh"
+
 namespace raster {
 
 constexpr unsigned long long kEmptyKey = 0x8000000000000000ull;
@@ -37,14 +39,6 @@ struct __align__(16) Slot {
     unsigned int aux;  // significant index during agglomeration, then label code
 };
 
-// Projection parameters derived once on the host from the scale s.
-struct ProjParams {
-    unsigned long long s_odd;  // odd part of the significand of s
-    int s_exp;                 // s = s_odd * 2^s_exp
-    int s_bits;                // bit length of s_odd
-    double scale;              // s itself, for the rare FP64 path
-};
-
 __device__ __forceinline__ unsigned long long pack_key(int ix, int iy) {
     return ((unsigned long long)(unsigned int)ix << 32) | (unsigned long long)(unsigned int)iy;
 }
@@ -57,82 +51,6 @@ __device__ __forceinline__ unsigned long long order_of(unsigned long long k) {
 }
 __device__ __forceinline__ unsigned long long key_of_order(unsigned long long o) {
     return o ^ 0x8000000080000000ull;
-}
-
-// Rare path: the definition itself on the FP64 pipe.
-__device__ __noinline__ bool project_coord_fp64(double v, double scale, int* out) {
-    double f = floor(__dmul_rn(v, scale));
-    if (!(f >= -2147483647.0 && f <= 2147483646.0)) return false;
-    *out = (int)f;
-    return true;
-}
-
-// floor(RN(v * s)) for one coordinate.  WIDE selects the 128-bit product
-// (s_odd wider than 11 bits, e.g. s = 10^3.5); otherwise v's significand times
-// s_odd fits in 64 bits (all integer precisions 0..4).
-template <bool WIDE>
-__device__ __forceinline__ bool project_coord(double v, const ProjParams& pp, int* out) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned int e = (unsigned int)(b >> 52) & 0x7FFu;
-    if (e - 1u >= 0x7FEu) {  // zero, subnormal, inf or nan
-        if ((b << 1) == 0) {  // +-0 projects to tile 0
-            *out = 0;
-            return true;
-        }
-        return project_coord_fp64(v, pp.scale, out);
-    }
-    const unsigned long long mx = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
-    // Exact product P = mx * s_odd, then its 53-bit rounding M (ties to even)
-    // and the exponent kk of M: RN(v*s) = +-M * 2^kk.
-    unsigned long long M;
-    int kk;
-    if (!WIDE) {
-        const unsigned long long P = mx * pp.s_odd;  // < 2^64
-        const int top = 52 + pp.s_bits;               // P has top or top+1 bits
-        const int t = top + (int)((P >> top) != 0ull);
-        const int r = t - 53;                         // discarded low bits, 0..11
-        if (r > 0) {
-            const unsigned long long lsb = (P >> r) & 1ull;
-            M = (P + (1ull << (r - 1)) - 1ull + lsb) >> r;
-        } else {
-            M = P;
-        }
-        kk = (int)e - 1075 + pp.s_exp + r;
-    } else {
-        const unsigned long long lo = mx * pp.s_odd;
-        const unsigned long long hi = __umul64hi(mx, pp.s_odd);
-        const int top = 52 + pp.s_bits;  // 64..105
-        const int t = top + (int)((top >= 64) ? ((hi >> (top - 64)) != 0ull) : ((hi != 0ull) || ((lo >> top) != 0ull)));
-        const int r = t - 53;            // 11..53
-        // M = P >> r, with round bit r-1 and sticky bits below it (all in lo)
-        unsigned long long q = (hi << (64 - r)) | (lo >> r);
-        const unsigned long long rb = (lo >> (r - 1)) & 1ull;
-        const unsigned long long sticky = (lo & ((1ull << (r - 1)) - 1ull)) != 0ull;
-        q += rb & (sticky | (q & 1ull));
-        M = q;
-        kk = (int)e - 1075 + pp.s_exp + r;
-    }
-    // M in [2^52, 2^53]; the rounding above assumed a normal result.
-    if (kk < -1074) return project_coord_fp64(v, pp.scale, out);
-    const int D = -kk;  // fractional bits of M
-    if (D <= 0) return false;  // |q| >= 2^52: outside the int32 tile range
-    unsigned long long ipart, frac;
-    if (D >= 64) {
-        ipart = 0ull;
-        frac = 1ull;
-    } else {
-        ipart = M >> D;
-        frac = (M << (64 - D)) != 0ull;
-    }
-    if (b >> 63) {  // negative: floor(-a) = -(ipart + (frac != 0))
-        const unsigned long long mag = ipart + frac;
-        if (mag > 2147483647ull) return false;
-        *out = -(int)mag;
-    } else {
-        if (ipart > 2147483646ull) return false;
-        *out = (int)ipart;
-    }
-    return true;
 }
 
 template <bool WIDE>
@@ -184,6 +102,56 @@ __device__ __forceinline__ int table_add(Slot* tab, unsigned int mask, unsigned 
         i = (i + 1u) & mask;
     }
     return -1;
+}
+
+// Insert continuing from a first probe whose key was already loaded (k at
+// slot i).  Used when a warp issues the first probes of several points at
+// once so that their DRAM latencies overlap.
+__device__ __forceinline__ int table_add_from(Slot* tab, unsigned int mask, unsigned long long key, unsigned int c,
+                                              unsigned int i, unsigned long long k, unsigned int max_probe) {
+    for (unsigned int p = 0; p < max_probe; ++p) {
+        if (k == key) {
+            atomicAdd(&tab[i].count, c);
+            return 0;
+        }
+        if (k == kEmptyKey) {
+            k = atomicCAS(&tab[i].key, kEmptyKey, key);
+            if (k == kEmptyKey) {
+                atomicAdd(&tab[i].count, c);
+                return 1;
+            }
+            if (k == key) {
+                atomicAdd(&tab[i].count, c);
+                return 0;
+            }
+        }
+        i = (i + 1u) & mask;
+        k = __ldcg(&tab[i].key);
+    }
+    return -1;
+}
+
+// Whole-slot load through L2 (16 bytes: key, count, aux).
+__device__ __forceinline__ Slot load_slot(const Slot* s) {
+    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+    Slot r;
+    r.key = v.x;
+    r.count = (unsigned int)v.y;
+    r.aux = (unsigned int)(v.y >> 32);
+    return r;
+}
+
+// Lookup continuing from a loaded first-probe slot `sl` at index i; returns
+// the matching slot, or one whose key is kEmptyKey when absent.
+__device__ __forceinline__ Slot table_find_from(const Slot* tab, unsigned int mask, unsigned long long key,
+                                                unsigned int i, Slot sl, unsigned int max_probe) {
+    for (unsigned int p = 0; p < max_probe; ++p) {
+        if (sl.key == key || sl.key == kEmptyKey) return sl;
+        i = (i + 1u) & mask;
+        sl = load_slot(&tab[i]);
+    }
+    sl.key = kEmptyKey;
+    return sl;
 }
 
 // Slot index of `key`, or -1 if absent.

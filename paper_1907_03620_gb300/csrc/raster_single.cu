@@ -215,18 +215,28 @@ __global__ void k_hook(const unsigned long long* d_nsig, const unsigned long lon
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned int st = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += stride) {
-        const unsigned long long key = sig_key[i];
+        const unsigned long long key = __ldcs(sig_key + i);
         const long long x = key_x(key), y = key_y(key);
-        // forward neighbours: (x+1, y-1), (x+1, y), (x+1, y+1), (x, y+1)
+        // forward neighbours: (x+1, y-1), (x+1, y), (x+1, y+1), (x, y+1); their
+        // first probes are issued together
+        unsigned long long nk[4];
+        unsigned int ns[4];
+        Slot sl[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const long long nx = x + (q < 3 ? 1 : 0);
             const long long ny = y + (q < 3 ? q - 1 : 1);
-            if (nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll) continue;
-            const long long s = table_find(tab, mask, pack_key((int)nx, (int)ny), max_probe);
-            if (s < 0) continue;
-            const Slot nb = tab[s];
-            if (nb.count < tau) continue;
+            const bool valid = !(nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll);
+            nk[q] = valid ? pack_key((int)nx, (int)ny) : kInvalidKey;
+            ns[q] = tile_hash(nk[q]) & mask;
+            if (valid) sl[q] = load_slot(&tab[ns[q]]);
+            else sl[q].key = kEmptyKey;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (nk[q] == kInvalidKey) continue;
+            const Slot nb = table_find_from(tab, mask, nk[q], ns[q], sl[q], max_probe);
+            if (nb.key != nk[q] || nb.count < tau) continue;
             if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
         }
     }
@@ -581,8 +591,10 @@ int make_proj_params(double scale, ProjParams* pp, bool* wide) {
     pp->s_odd = m;
     pp->s_exp = e - 1075 + tz;
     pp->s_bits = bits;
+    pp->d0 = 1075 - pp->s_exp;
+    pp->top = 52 + bits;
     pp->scale = scale;
-    *wide = bits > 11;
+    *wide = bits > 10;
     return RASTER_OK;
 }
 
