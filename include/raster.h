@@ -51,6 +51,7 @@ extern "C" {
 #define RASTER_E_CUDA 5        /* a CUDA runtime call failed */
 #define RASTER_E_INTERNAL 6    /* a bounded device iteration did not converge */
 #define RASTER_E_STATE 7       /* call not valid in the handle's state (e.g. labels before agglomerate) */
+#define RASTER_E_LIMIT 8       /* input larger than a fixed capacity (raster_count_tiles_static) */
 
 #define RASTER_NOISE INT64_MIN /* label of a point outside every kept cluster */
 
@@ -137,6 +138,34 @@ uint64_t raster_kernel_launches(void);
 
 /* Release the handle and its device memory (synchronises). */
 int raster_destroy(raster_handle *h);
+
+/* Largest input accepted by raster_count_tiles_static. */
+#define RASTER_STATIC_MAX_POINTS 524288
+
+/* Tile counts without any allocation -- the paper has no counterpart; this is
+ * for callers that cannot allocate device memory (code running inside another
+ * runtime's memory pool or a fixed memory budget, plugins whose host owns all
+ * allocations, paths that must avoid the allocator's implicit synchronisation).
+ *
+ * Projects the n points at DEVICE xy (interleaved float64 pairs, 16-byte
+ * aligned) with s = 10^precision exactly like raster_contract and writes every
+ * tile holding at least one point as a row (key, count) into the caller's
+ * DEVICE arrays key_out and count_out, which must have room for n rows (a tile
+ * count never exceeds n).  Row order is unspecified.  *n_tiles_out (HOST)
+ * receives the number of rows.  Synchronises `stream` before returning.
+ *
+ * The hash table is a fixed 16 MiB array of device memory inside the library
+ * (present on every GPU that loads the library, until the process exits); no
+ * cudaMalloc, cudaFree or other allocating call is made.  n larger than
+ * RASTER_STATIC_MAX_POINTS returns RASTER_E_LIMIT and does nothing.  The first
+ * call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the array and each clears it first: calls whose GPU work
+ * overlaps (other streams or host threads) race and must be serialised.
+ * Returns RASTER_E_RANGE if some point was skipped (non-finite or out of the
+ * int32 tile range), RASTER_E_ARG for bad arguments. */
+int raster_count_tiles_static(const double *xy, int64_t n, double precision, int64_t *key_out,
+                              uint32_t *count_out, int64_t *n_tiles_out, void *stream);
 
 /* Static description of a status code. */
 const char *raster_strerror(int status);

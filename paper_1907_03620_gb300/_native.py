@@ -17,10 +17,11 @@ _lock = threading.Lock()
 _lib = None
 
 OK = 0
-E_ARG, E_RANGE, E_OOM, E_TABLE_FULL, E_CUDA, E_INTERNAL, E_STATE = 1, 2, 3, 4, 5, 6, 7
+E_ARG, E_RANGE, E_OOM, E_TABLE_FULL, E_CUDA, E_INTERNAL, E_STATE, E_LIMIT = 1, 2, 3, 4, 5, 6, 7, 8
+STATIC_MAX_POINTS = 524288
 NOISE = -(2 ** 63)
 NAMES = {0: "RASTER_OK", 1: "RASTER_E_ARG", 2: "RASTER_E_RANGE", 3: "RASTER_E_OOM", 4: "RASTER_E_TABLE_FULL",
-         5: "RASTER_E_CUDA", 6: "RASTER_E_INTERNAL", 7: "RASTER_E_STATE"}
+         5: "RASTER_E_CUDA", 6: "RASTER_E_INTERNAL", 7: "RASTER_E_STATE", 8: "RASTER_E_LIMIT"}
 
 
 class RasterError(RuntimeError):
@@ -66,6 +67,7 @@ def _declare(L):
         "raster_table_capacity": (i64, [vp]),
         "raster_destroy": (ci, [vp]),
         "raster_kernel_launches": (ctypes.c_uint64, []),
+        "raster_count_tiles_static": (ci, [vp, i64, dbl, vp, vp, ctypes.POINTER(i64), vp]),
         "raster_strerror": (ctypes.c_char_p, [ci]),
     }
     for name, (res, args) in sig.items():

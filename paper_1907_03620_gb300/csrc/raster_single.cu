@@ -622,6 +622,7 @@ const char* raster_strerror(int status) {
         case RASTER_E_CUDA: return "CUDA runtime error";
         case RASTER_E_INTERNAL: return "bounded device iteration did not converge";
         case RASTER_E_STATE: return "call not valid in the handle's current state";
+        case RASTER_E_LIMIT: return "input larger than the fixed capacity of this entry point";
         default: return "unknown status";
     }
 }
