@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="points of the oracle sample")
     ap.add_argument("--profile", action="store_true", help="short run for ncu (no clocks/e2e/cpu legs)")
     ap.add_argument("--points", type=int, default=0, help="use only the first N points (profiling cases)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--loop-seconds", type=float, default=15.0, help="time budget of the single-call loop baseline")
     return ap.parse_args()
 
 
@@ -174,6 +176,77 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+
+def batched_leg(args, dev):
+    """Batched form: the 4096-instance workload in one graph launch, against a
+    loop of plain single-instance calls (create, contract, agglomerate,
+    destroy) on the same GPU."""
+    import torch
+
+    import paper_1907_03620_gb300 as R
+    from paper_1907_03620_gb300 import tune
+    from paper_1907_03620_gb300.batch import RasterBatch
+
+    ws = gen.batch_instances()
+    offs = np.cumsum([0] + [w.n for w in ws])
+    total = int(offs[-1])
+    flat = torch.empty((total, 2), dtype=torch.float64, device=dev)
+    host = np.empty((int(max(w.n for w in ws)), 2), dtype=np.float64)
+    for i, w in enumerate(ws):
+        gen.points_into(host[: w.n], w)
+        flat[offs[i]:offs[i + 1]].copy_(torch.from_numpy(host[: w.n]))
+    inst = [(flat[offs[i]:offs[i + 1]], w.precision, w.tau, w.mu) for i, w in enumerate(ws)]
+    t0 = time.perf_counter()
+    cfg = tune.tune_batch(inst)
+    tune_s = time.perf_counter() - t0
+    b = RasterBatch(inst, **cfg)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 1)):
+        b.run()
+    b.wait()
+    times = []
+    for _ in range(max(args.steps, 3)):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        b.run()
+        s1.record(stream)
+        b.wait()
+        times.append(s0.elapsed_time(s1))
+    ms = statistics.mean(times)
+    launches_per_run = 9
+    n_clusters = sum(b.counts(i).n_clusters for i in range(len(ws)))
+    dev_bytes = b.device_bytes
+    b.close()
+    # loop of plain single-instance calls, time-bounded, over a fixed order
+    lat, pts = [], 0
+    order = list(range(len(ws)))
+    t_loop0 = time.perf_counter()
+    torch.cuda.synchronize()
+    for i in order:
+        t1 = time.perf_counter()
+        r = R.Raster(ws[i].precision, ws[i].tau, ws[i].mu)
+        r.contract(inst[i][0])
+        r.agglomerate(copy=False)
+        r.close()
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - t1) * 1e3)
+        pts += ws[i].n
+        if time.perf_counter() - t_loop0 > args.loop_seconds:
+            break
+    loop_rate = pts / (sum(lat) / 1e3)
+    del flat
+    torch.cuda.empty_cache()
+    q = lambda v, p: float(np.percentile(np.array(v), p))  # noqa: E731
+    return {"metric": "points_per_s", "value": total / (ms / 1e3), "unit": "points/s",
+            "instances": len(ws), "points": total, "ms_per_run": ms, "runs": len(times),
+            "latency_p50_ms": q(times, 50), "latency_p99_ms": q(times, 99),
+            "clusters": n_clusters, "device_bytes": dev_bytes, "config": cfg, "tune_seconds": tune_s,
+            "gpu_launches_per_run": launches_per_run,
+            "loop_baseline": {"value": loop_rate, "unit": "points/s", "instances": len(lat), "points": pts,
+                              "latency_p50_ms": q(lat, 50), "latency_p99_ms": q(lat, 99),
+                              "calls": "create, contract, agglomerate, destroy per instance"},
+            "speedup_vs_loop": (total / (ms / 1e3)) / loop_rate}
+
 
 def run_gpu(args):
     import torch
@@ -310,6 +383,10 @@ def run_gpu(args):
                                 "sample": desc, "seconds": dt}
 
     r.close()
+    del xy, labels, host
+    torch.cuda.empty_cache()
+    if not args.no_forms and not args.profile:
+        line["batched"] = batched_leg(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

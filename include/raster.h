@@ -92,7 +92,8 @@ int raster_reserve(raster_handle *h, int64_t n_tiles);
  * to grow.  The total number of points per handle must stay below 2^32. */
 int raster_contract(raster_handle *h, const double *xy, int64_t n, void *stream);
 
-/* As raster_contract, but xy is in HOST memory (pinned for full speed).  The
+/* Contraction of one chunk (Alg. 1 first loop; Sect. 3.6) as raster_contract,
+ * but xy is in HOST memory (pinned for full speed).  The
  * points are streamed through device staging buffers, copies overlapping the
  * contraction.  Returns once xy may be reused (synchronous). */
 int raster_contract_host(raster_handle *h, const double *xy_host, int64_t n, void *stream);
@@ -110,34 +111,95 @@ int raster_agglomerate(raster_handle *h, raster_clusters *out);
  * caller-owned.  Asynchronous on `stream`. */
 int raster_point_labels(raster_handle *h, const double *xy, int64_t n, int64_t *labels, void *stream);
 
-/* As raster_point_labels with HOST xy and HOST labels; synchronous. */
+/* Per-point labels (RASTER*, Sect. 4.1) as raster_point_labels, with HOST xy
+ * and HOST labels; synchronous. */
 int raster_point_labels_host(raster_handle *h, const double *xy_host, int64_t n, int64_t *labels_host,
                              void *stream);
 
-/* Copy every tile with at least one point (key, count) into caller DEVICE
- * buffers of `capacity` rows; *n_out receives D.  Order unspecified.
+/* The tile table after contraction (acc of Alg. 1): copy every tile with at
+ * least one point (key, count) into caller DEVICE buffers of `capacity` rows;
+ * *n_out receives D.  Order unspecified.
  * Returns RASTER_E_ARG if capacity < D (nothing is written then).
  * Synchronises.  Used for checkpointing and for tests. */
 int raster_export_tiles(raster_handle *h, int64_t *key, uint32_t *count, int64_t capacity, int64_t *n_out);
 
-/* Forget all points (keep the table's capacity) on `stream`; clears errors. */
+/* Forget all points (keep the table's capacity) on `stream`; clears errors.
+ * Lifecycle call; no counterpart in the paper. */
 int raster_reset(raster_handle *h, void *stream);
 
-/* Synchronise and return the handle's recorded status (RASTER_OK if none). */
+/* Synchronise and return the handle's recorded status (RASTER_OK if none).
+ * Diagnostics; no counterpart in the paper. */
 int raster_status(raster_handle *h);
 
-/* The scale s = 10^precision used for projection (one double). */
+/* The scale s = 10^precision used by project() (Alg. 1; Sect. 3.2), as the one
+ * double both the kernels and any checker must multiply by. */
 double raster_get_scale(const raster_handle *h);
 
-/* Table capacity in slots (for diagnostics). */
+/* Table capacity in slots.  Diagnostics; no counterpart in the paper. */
 int64_t raster_table_capacity(const raster_handle *h);
 
 /* Number of kernels this library has launched in this process, over all
- * handles (diagnostics: lets a caller count device launches in a region). */
+ * handles (lets a caller count device launches in a region).  Diagnostics;
+ * no counterpart in the paper. */
 uint64_t raster_kernel_launches(void);
 
-/* Release the handle and its device memory (synchronises). */
+/* Release the handle and its device memory (synchronises).  Lifecycle call;
+ * no counterpart in the paper. */
 int raster_destroy(raster_handle *h);
+
+/* ---- Batched form: many independent instances, one graph launch ----------
+ *
+ * Runs contraction and agglomeration (Alg. 1) for `count` independent RASTER
+ * problems at once, each with its own points, precision, tau and mu.  All
+ * instances share one persistent contraction kernel and one sequence of
+ * segmented agglomeration kernels, captured once in a CUDA graph at creation
+ * and replayed by every raster_batch_run.  Each instance's result is exactly
+ * what a separate handle would produce.  (Per-point labels are not part of
+ * the batched form.) */
+typedef struct {
+    const double *xy;  /* DEVICE, n x 2 interleaved float64, 16-byte aligned; must stay
+                          valid and hold the instance's points whenever the batch runs */
+    int64_t n;         /* points, >= 0 */
+    double precision;  /* tile side 10^-precision */
+    uint32_t tau, mu;  /* >= 1 */
+} raster_instance;
+
+/* Tuning knobs (0 / -1 = default).  None of them changes any result. */
+typedef struct {
+    double load;     /* table slots >= n_i / load (power of two), 0 < load <= 0.75 */
+    int32_t block;   /* threads per block of the contraction kernel: 128, 256 or 512 */
+    int32_t width;   /* points per thread per iteration: 1, 2, 4 or 8 */
+    int32_t preagg;  /* 1: merge equal tiles within a warp before inserting; 0: off */
+} raster_batch_config;
+
+typedef struct raster_batch raster_batch;
+
+/* Plan the batch of Alg. 1 problems (sizes every table from its n, so no table
+ * can overflow), allocate its device memory and capture its graph on the
+ * current device.  inst[] is copied; the xy pointers are baked into the graph.
+ * RASTER_E_ARG for an invalid instance or knob. */
+int raster_batch_create(const raster_instance *inst, int32_t count, const raster_batch_config *cfg,
+                        raster_batch **out);
+
+/* Run contraction and agglomeration (Alg. 1) of every instance on `stream`
+ * (asynchronous: one graph launch). */
+int raster_batch_run(raster_batch *b, void *stream);
+
+/* Wait for the last run; returns the worst status over all instances.
+ * Synchronisation call; no counterpart in the paper. */
+int raster_batch_wait(raster_batch *b);
+
+/* Clusters (Alg. 1 output) of instance i of the last run, after
+ * raster_batch_wait: DEVICE arrays owned by the batch, valid until its next
+ * run or destroy.  Returns that instance's own status. */
+int raster_batch_result(raster_batch *b, int32_t i, raster_clusters *out);
+
+/* Device bytes held by the batch (tables, scratch and results).  Diagnostics;
+ * no counterpart in the paper. */
+int64_t raster_batch_device_bytes(const raster_batch *b);
+
+/* Release the batch.  Lifecycle call; no counterpart in the paper. */
+int raster_batch_destroy(raster_batch *b);
 
 /* Largest input accepted by raster_count_tiles_static. */
 #define RASTER_STATIC_MAX_POINTS 524288
@@ -167,7 +229,7 @@ int raster_destroy(raster_handle *h);
 int raster_count_tiles_static(const double *xy, int64_t n, double precision, int64_t *key_out,
                               uint32_t *count_out, int64_t *n_tiles_out, void *stream);
 
-/* Static description of a status code. */
+/* Static description of a status code.  No counterpart in the paper. */
 const char *raster_strerror(int status);
 
 #ifdef __cplusplus

@@ -31,6 +31,16 @@ class RasterError(RuntimeError):
         super().__init__(f"{where}: {NAMES.get(status, status)} ({msg})")
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("n", ctypes.c_int64), ("precision", ctypes.c_double),
+                ("tau", ctypes.c_uint32), ("mu", ctypes.c_uint32)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("load", ctypes.c_double), ("block", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("preagg", ctypes.c_int32)]
+
+
 class Clusters(ctypes.Structure):
     _fields_ = [("key", ctypes.c_void_p), ("count", ctypes.c_void_p), ("cid", ctypes.c_void_p),
                 ("n_tiles", ctypes.c_int64), ("n_clusters", ctypes.c_int64), ("n_distinct", ctypes.c_int64),
@@ -69,6 +79,13 @@ def _declare(L):
         "raster_kernel_launches": (ctypes.c_uint64, []),
         "raster_count_tiles_static": (ci, [vp, i64, dbl, vp, vp, ctypes.POINTER(i64), vp]),
         "raster_strerror": (ctypes.c_char_p, [ci]),
+        "raster_batch_create": (ci, [ctypes.POINTER(Instance), ctypes.c_int32, ctypes.POINTER(BatchConfig),
+                                     ctypes.POINTER(vp)]),
+        "raster_batch_run": (ci, [vp, vp]),
+        "raster_batch_wait": (ci, [vp]),
+        "raster_batch_result": (ci, [vp, ctypes.c_int32, ctypes.POINTER(Clusters)]),
+        "raster_batch_device_bytes": (i64, [vp]),
+        "raster_batch_destroy": (ci, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -33,6 +33,7 @@
 #include "../../include/raster.h"
 #include "raster_device.cuh"
 #include "raster_host.h"
+#include "raster_block.cuh"
 
 using namespace raster;
 
@@ -48,46 +49,6 @@ constexpr int kUnionLimit = 1 << 30;
 
 // ---------------------------------------------------------------------------
 // Block helpers
-
-__device__ __forceinline__ unsigned int warp_incl_scan(unsigned int v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned int t = __shfl_up_sync(0xFFFFFFFFu, v, d);
-        if (lane >= d) v += t;
-    }
-    return v;
-}
-
-// Exclusive block scan of v (blockDim.x == kBlock); returns the prefix and
-// writes the block total to *total.  Uses `scratch` (>= 33 words).
-__device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned int* scratch, unsigned int* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned int incl = warp_incl_scan(v);
-    if (lane == 31) scratch[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned int w = (lane < (kBlock >> 5)) ? scratch[lane] : 0u;
-        const unsigned int wi = warp_incl_scan(w);
-        if (lane < (kBlock >> 5)) scratch[lane] = wi - w;
-        if (lane == (kBlock >> 5) - 1) scratch[32] = wi;
-    }
-    __syncthreads();
-    const unsigned int r = scratch[warp] + incl - v;
-    *total = scratch[32];
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ void flush_counts(unsigned int newk, unsigned int st, unsigned long long* d_newkeys,
-                                             unsigned int* d_status) {
-    newk = __reduce_add_sync(0xFFFFFFFFu, newk);
-    st = __reduce_or_sync(0xFFFFFFFFu, st);
-    if ((threadIdx.x & 31) == 0) {
-        if (newk) atomicAdd(d_newkeys, (unsigned long long)newk);
-        if (st) atomicOr(d_status, st);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Kernels

@@ -21,17 +21,18 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_every_declaration_cites_its_source_or_says_it_has_none():
-    """Each entry point's comment names the passage that defines it."""
+    """The comment just above each entry point names the paper passage that
+    defines the operation, or says that the paper has no counterpart."""
+    cite = re.compile(r"Alg\. \d|Sect\. \d|App\. [A-D]|no counterpart in the paper|paper has no counterpart", re.I)
     for fn in os.listdir(os.path.join(ROOT, "include")):
         src = open(os.path.join(ROOT, "include", fn)).read()
-        blocks = re.split(r"\n\s*\n", src)
-        for b in blocks:
-            for name in re.findall(r"\b(raster_[a-z0-9_]+)\s*\(", b):
-                if "/*" not in b:
-                    continue
-                assert re.search(r"(Alg\. \d|Sect\. \d|App\. [A-D]|paper has no counterpart|no counterpart"
-                                 r"|diagnostics|Static description|Release the handle|Synchronise and return|"
-                                 r"scale s|status|Forget all|Copy every tile|As raster_)", b), (fn, name)
+        for m in re.finditer(r"^(?:const\s+)?[a-z_0-9]+\s*\**\s*(raster_[a-z0-9_]+)\s*\(", src, flags=re.M):
+            before = src[:m.start()]
+            end = before.rstrip().rfind("*/")
+            assert end >= 0 and before.rstrip().endswith("*/"), f"{m.group(1)} has no comment"
+            start = before.rfind("/*", 0, end)
+            comment = " ".join(before[start:end].split())
+            assert cite.search(comment), f"{m.group(1)}: {comment[:80]}"
 
 
 def test_strerror_and_argument_checks_without_gpu():
