@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--points", type=int, default=0, help="use only the first N points (profiling cases)")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served legs")
     ap.add_argument("--loop-seconds", type=float, default=15.0, help="time budget of the single-call loop baseline")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="duration of each Poisson serving run")
+    ap.add_argument("--serve-rates", default="0.8", help="arrival rates as fractions of saturated throughput")
     return ap.parse_args()
 
 
@@ -248,6 +250,135 @@ def batched_leg(args, dev):
             "speedup_vs_loop": (total / (ms / 1e3)) / loop_rate}
 
 
+def served_leg(args, dev):
+    """Served form: Poisson arrivals of requests (sizes log-uniform 1e4..2e7,
+    1..8 chunks each, per-request p/tau/mu) into the continuous-batching
+    engine.  Request data comes from a pool of pre-staged device workloads."""
+    import torch
+
+    import paper_1907_03620_gb300 as R
+    from paper_1907_03620_gb300.serve import RasterServer
+
+    pool_n = 48
+    pool = []
+    for i in range(pool_n):
+        w = gen._instance(5, i, gen._log_uniform_size(5, i, 10_000, 20_000_000), 0.10)
+        chunks = 1 + gen.rng_at(5, 15, i) % 8
+        xy = torch.from_numpy(gen.points(w)).to(dev)
+        views = [xy[lo:hi] for lo, hi in gen.chunk_bounds(w.n, int(chunks))]
+        pool.append((w, xy, views))
+    srv = RasterServer(table_slots=1 << 32, result_rows=1 << 28, max_active=4096)
+    done_lat, done_pts = [], [0]
+    lock = threading.Lock()
+    stop = [False]
+
+    def poller():
+        while not stop[0]:
+            r = srv.poll(wait_ms=20, copy=False)
+            if r is None:
+                continue
+            rid, res, lat = r
+            srv.release(rid)
+            with lock:
+                done_lat.append(lat)
+                done_pts[0] += res.n_points
+
+    def submit(rid, k):
+        w, xy, views = pool[k % pool_n]
+        srv.submit(rid, w.precision, w.tau, w.mu, w.n, len(views))
+        for v in views:
+            srv.push(rid, v)
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    # saturation: a burst of requests submitted at once
+    burst = 4 * pool_n
+    for k in range(pool_n):  # warm-up pass
+        submit(10**9 + k, k)
+    while True:
+        with lock:
+            if len(done_lat) >= pool_n:
+                break
+        time.sleep(0.01)
+    with lock:
+        done_lat.clear()
+        done_pts[0] = 0
+    t0 = time.perf_counter()
+    for k in range(burst):
+        submit(k, k)
+    while True:
+        with lock:
+            if len(done_lat) >= burst:
+                break
+        time.sleep(0.002)
+    t_sat = time.perf_counter() - t0
+    with lock:
+        sat_pts = done_pts[0]
+        done_lat.clear()
+        done_pts[0] = 0
+    sat_rate = sat_pts / t_sat
+    mean_pts = sat_pts / burst
+    runs = []
+    rid = 10**6
+    for frac in [float(f) for f in args.serve_rates.split(",") if f]:
+        req_rate = frac * sat_rate / mean_pts
+        arrivals = gen.serve_requests(rate_per_s=req_rate, duration_s=args.serve_seconds, seed=7)
+        with lock:
+            done_lat.clear()
+            done_pts[0] = 0
+        t0 = time.perf_counter()
+        for k, rq in enumerate(arrivals):
+            delay = rq.arrival_s - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            submit(rid, k)
+            rid += 1
+        while True:
+            with lock:
+                if len(done_lat) >= len(arrivals):
+                    break
+            time.sleep(0.002)
+        wall = time.perf_counter() - t0
+        with lock:
+            lat = list(done_lat)
+            pts = done_pts[0]
+        runs.append({"load_fraction": frac, "requests": len(arrivals), "offered_req_per_s": req_rate,
+                     "points_per_s": pts / wall, "latency_p50_ms": float(np.percentile(lat, 50)),
+                     "latency_p99_ms": float(np.percentile(lat, 99)), "seconds": wall})
+    stop[0] = True
+    th.join()
+    st = srv.stats()
+    srv.close()
+    # FIFO loop of plain single-instance calls over the same request mix
+    loop_lat, loop_pts = [], 0
+    t_loop = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t_loop < args.loop_seconds and k < 4 * pool_n:
+        w, xy, views = pool[k % pool_n]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h = R.Raster(w.precision, w.tau, w.mu)
+        for v in views:
+            h.contract(v)
+        h.agglomerate(copy=False)
+        h.close()
+        torch.cuda.synchronize()
+        loop_lat.append((time.perf_counter() - t1) * 1e3)
+        loop_pts += w.n
+        k += 1
+    loop_rate = loop_pts / (sum(loop_lat) / 1e3)
+    del pool
+    torch.cuda.empty_cache()
+    return {"metric": "points_per_s", "saturated_points_per_s": sat_rate, "saturated_burst_requests": burst,
+            "mean_request_points": mean_pts, "runs": runs, "engine_steps": st["steps"],
+            "loop_baseline": {"value": loop_rate, "unit": "points/s", "requests": len(loop_lat),
+                              "latency_p50_ms": float(np.percentile(loop_lat, 50)),
+                              "latency_p99_ms": float(np.percentile(loop_lat, 99)),
+                              "calls": "FIFO: create, contract per chunk, agglomerate, destroy per request"},
+            "speedup_vs_loop": sat_rate / loop_rate,
+            "request_data": f"pool of {pool_n} pre-staged device workloads, request k uses pool[k % {pool_n}]"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -387,6 +518,7 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     if not args.no_forms and not args.profile:
         line["batched"] = batched_leg(args, dev)
+        line["served"] = served_leg(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

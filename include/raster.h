@@ -201,6 +201,64 @@ int64_t raster_batch_device_bytes(const raster_batch *b);
 /* Release the batch.  Lifecycle call; no counterpart in the paper. */
 int raster_batch_destroy(raster_batch *b);
 
+/* ---- Served form: continuous batching of requests ------------------------
+ *
+ * A serving engine with a worker thread.  Requests (one Alg. 1 problem each)
+ * arrive at any time and send their points in chunks (chunked processing,
+ * Sect. 3.6).  Every step the engine admits waiting requests in arrival order
+ * while its device arenas can hold the request's tile table and result rows,
+ * contracts every ready chunk of every admitted request in one segmented
+ * launch, and agglomerates every request whose chunks are all in.  Requests
+ * therefore overlap on the device; each result equals that of a separate
+ * handle. */
+typedef struct raster_server raster_server;
+
+typedef struct {
+    int64_t table_slots;  /* tile-table arena, 16-byte slots (a request of n points takes a power
+                             of two >= n / 0.75, at least 4096) */
+    int64_t result_rows;  /* result arena rows (a request takes max(1, n / tau)) */
+    int32_t max_active;   /* most requests admitted at once */
+} raster_server_config;
+
+typedef struct {
+    int64_t steps, points, waiting, active, completed_unpolled, table_slots_used, result_rows_used;
+} raster_server_stats_t;
+
+/* Allocate the arenas on the current device and start the worker thread.
+ * RASTER_E_ARG for a bad config, RASTER_E_OOM if the arenas do not fit.
+ * Lifecycle call; no counterpart in the paper. */
+int raster_server_create(const raster_server_config *cfg, raster_server **out);
+
+/* Announce request `request_id` (unique among live requests): an Alg. 1
+ * problem of n_total points in n_chunks chunks.  Returns RASTER_E_LIMIT if it
+ * could never fit the arenas.  Thread-safe. */
+int raster_server_submit(raster_server *s, int64_t request_id, double precision, uint32_t tau, uint32_t mu,
+                         int64_t n_total, int32_t n_chunks);
+
+/* Give the next chunk of a request (chunked contraction, Sect. 3.6): DEVICE
+ * xy, n x 2 float64, 16-byte aligned, caller-owned, valid until the request
+ * completes.  The chunk sizes must add up to n_total.  Thread-safe. */
+int raster_server_push(raster_server *s, int64_t request_id, const double *xy, int64_t n);
+
+/* Take one completed request (Alg. 1 output), waiting up to wait_ms: its id,
+ * its clusters (DEVICE arrays in the engine's arena, valid until released) and
+ * its latency from submit to completion.  Returns the request's status, or
+ * RASTER_E_STATE when none completed in time.  Thread-safe. */
+int raster_server_poll(raster_server *s, int32_t wait_ms, int64_t *request_id, raster_clusters *out,
+                       double *latency_ms);
+
+/* Free a completed request's table and rows.  Lifecycle call; no counterpart
+ * in the paper. */
+int raster_server_release(raster_server *s, int64_t request_id);
+
+/* Engine counters; returns the engine's fatal status (RASTER_OK if none).
+ * Diagnostics; no counterpart in the paper. */
+int raster_server_stats(raster_server *s, raster_server_stats_t *out);
+
+/* Stop the worker and free everything.  Lifecycle call; no counterpart in the
+ * paper. */
+int raster_server_destroy(raster_server *s);
+
 /* Largest input accepted by raster_count_tiles_static. */
 #define RASTER_STATIC_MAX_POINTS 524288
 

@@ -41,6 +41,15 @@ class BatchConfig(ctypes.Structure):
                 ("preagg", ctypes.c_int32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("table_slots", ctypes.c_int64), ("result_rows", ctypes.c_int64), ("max_active", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("steps", "points", "waiting", "active", "completed_unpolled",
+                                              "table_slots_used", "result_rows_used")]
+
+
 class Clusters(ctypes.Structure):
     _fields_ = [("key", ctypes.c_void_p), ("count", ctypes.c_void_p), ("cid", ctypes.c_void_p),
                 ("n_tiles", ctypes.c_int64), ("n_clusters", ctypes.c_int64), ("n_distinct", ctypes.c_int64),
@@ -86,6 +95,14 @@ def _declare(L):
         "raster_batch_result": (ci, [vp, ctypes.c_int32, ctypes.POINTER(Clusters)]),
         "raster_batch_device_bytes": (i64, [vp]),
         "raster_batch_destroy": (ci, [vp]),
+        "raster_server_create": (ci, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+        "raster_server_submit": (ci, [vp, i64, dbl, u32, u32, i64, ctypes.c_int32]),
+        "raster_server_push": (ci, [vp, i64, vp, i64]),
+        "raster_server_poll": (ci, [vp, ctypes.c_int32, ctypes.POINTER(i64), ctypes.POINTER(Clusters),
+                                    ctypes.POINTER(dbl)]),
+        "raster_server_release": (ci, [vp, i64]),
+        "raster_server_stats": (ci, [vp, ctypes.POINTER(ServerStats)]),
+        "raster_server_destroy": (ci, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -31,7 +31,7 @@ def test_every_declaration_cites_its_source_or_says_it_has_none():
             end = before.rstrip().rfind("*/")
             assert end >= 0 and before.rstrip().endswith("*/"), f"{m.group(1)} has no comment"
             start = before.rfind("/*", 0, end)
-            comment = " ".join(before[start:end].split())
+            comment = " ".join(before[start:end].replace("*", " ").split())
             assert cite.search(comment), f"{m.group(1)}: {comment[:80]}"
 
 
