@@ -88,8 +88,10 @@ int raster_reserve(raster_handle *h, int64_t n_tiles);
  * xy: DEVICE pointer to n points as interleaved float64 pairs (x0,y0,x1,y1,..),
  *   16-byte aligned; caller-owned and must stay valid until the stream work
  *   completes.  n >= 0.  Callable any number of times; counts accumulate.
- * Asynchronous on `stream`, except that it synchronises when the table has
- * to grow.  The total number of points per handle must stay below 2^32. */
+ * Work is enqueued on `stream`; the call synchronises once per 2^28 points
+ * to read the table's tile count (and grows the table when needed), so xy
+ * may be released when it returns.  The total number of points per handle
+ * must stay below 2^32. */
 int raster_contract(raster_handle *h, const double *xy, int64_t n, void *stream);
 
 /* Contraction of one chunk (Alg. 1 first loop; Sect. 3.6) as raster_contract,

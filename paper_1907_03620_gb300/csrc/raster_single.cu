@@ -34,6 +34,7 @@
 #include "raster_device.cuh"
 #include "raster_host.h"
 #include "raster_block.cuh"
+#include "raster_region.cuh"
 
 using namespace raster;
 
@@ -41,10 +42,11 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kContractUnroll = 4;
-constexpr double kMaxLoad = 0.75;     // a launch never pushes the table beyond this load
-constexpr double kGrowLoad = 0.7;     // target load after growing (before the next chunk)
-constexpr long long kMinStep = 1 << 20;
-constexpr long long kGrowStep = 64ll << 20;
+// Table load: lookups (neighbour probes, labels) touch fewer sectors in a
+// sparse table, which outweighs the larger clear and scan; measured best
+// around 0.25-0.35 on the 500M-point workload.
+constexpr double kMaxLoad = 0.5;      // grow after a round that leaves the table fuller than this
+constexpr double kGrowLoad = 0.3;     // target load after growing
 constexpr int kUnionLimit = 1 << 30;
 
 // ---------------------------------------------------------------------------
@@ -62,50 +64,232 @@ __global__ void k_fill_table(Slot* tab, unsigned long long cap) {
         reinterpret_cast<ulonglong2*>(tab)[i] = v;
 }
 
-template <bool WIDE, int U>
-__global__ void __launch_bounds__(kBlock) k_contract(const double2* __restrict__ xy, long long n, ProjParams pp,
-                                                    Slot* tab, unsigned int mask, unsigned int max_probe,
-                                                    unsigned long long* d_newkeys, unsigned int* d_status) {
-    const int lane = threadIdx.x & 31;
-    const long long warps_total = (long long)gridDim.x * (kBlock >> 5);
-    const long long per_warp = 32ll * U;
-    unsigned int newk = 0, st = 0;
-    for (long long base = ((long long)blockIdx.x * (kBlock >> 5) + (threadIdx.x >> 5)) * per_warp; base < n;
-         base += warps_total * per_warp) {
-        double2 p[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long i = base + u * 32 + lane;
-            if (i < n) p[u] = __ldcs(xy + i);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long i = base + u * 32 + lane;
-            unsigned long long key = kInvalidKey;
-            if (i < n) {
-                key = project_point<WIDE>(p[u].x, p[u].y, pp);
-                if (key == kInvalidKey) st |= kStRange;
-            }
-            const unsigned int grp = __match_any_sync(0xFFFFFFFFu, key);
-            if (lane == __ffs(grp) - 1 && key != kInvalidKey) {
-                const int r = table_add(tab, mask, key, (unsigned int)__popc(grp), max_probe);
-                if (r > 0)
-                    ++newk;
-                else if (r < 0)
-                    st |= kStFull;
-            }
-        }
+// Pass 1 of contraction: project a tile of kPartTile points, counting-sort the
+// keys by table region in shared memory, reserve space in each region's
+// staging segment with one atomic per (tile, region), and append the keys in
+// coalesced runs.  Keys beyond a segment's capacity (a region far above its
+// share) go to the overflow list.
+constexpr int kPartTile = 2048;
+constexpr int kPartPer = kPartTile / kBlock;
+constexpr long long kInsertItem = 1024;
+
+__device__ __forceinline__ unsigned int block_excl_scan_bins(unsigned int* bins, int nbins, unsigned int* start,
+                                                             unsigned int* scratch) {
+    // each thread owns a contiguous run of bins
+    const int per = (nbins + kBlock - 1) / kBlock;
+    const int b0 = threadIdx.x * per;
+    unsigned int sum = 0;
+    for (int b = b0; b < min(b0 + per, nbins); ++b) sum += bins[b];
+    unsigned int total;
+    unsigned int off = block_excl_scan(sum, scratch, &total);
+    for (int b = b0; b < min(b0 + per, nbins); ++b) {
+        start[b] = off;
+        off += bins[b];
     }
-    flush_counts(newk, st, d_newkeys, d_status);
+    __syncthreads();
+    return total;
 }
 
-__global__ void k_rehash(const Slot* __restrict__ old_tab, unsigned long long old_cap, Slot* tab, unsigned int mask,
-                         unsigned int max_probe, unsigned int* d_status) {
+// Append (key, c) to the overflow list (warp-aggregated); the list has room
+// for every key of a round, so it cannot overflow itself.
+__device__ __forceinline__ void overflow_append(bool want, unsigned long long key, unsigned int c,
+                                                unsigned long long* ovf_key, unsigned int* ovf_cnt,
+                                                unsigned long long* ovf_n) {
+    const unsigned int m = __ballot_sync(__activemask(), want);
+    if (!want) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(ovf_n, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+    ovf_key[pos] = key;
+    ovf_cnt[pos] = c;
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kBlock) k_part(const double2* __restrict__ xy, long long n, ProjParams pp,
+                                                RegionTable t, unsigned long long* __restrict__ stage,
+                                                unsigned long long seg_cap, unsigned int* __restrict__ cursor,
+                                                unsigned long long* ovf_key, unsigned int* ovf_cnt,
+                                                unsigned long long* ovf_n, unsigned int* d_status) {
+    extern __shared__ unsigned char smem[];
+    unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(smem);   // kPartTile
+    unsigned long long* s_sorted = s_keys + kPartTile;                           // kPartTile
+    unsigned int* s_meta = reinterpret_cast<unsigned int*>(s_sorted + kPartTile); // kPartTile
+    unsigned int* s_fill = s_meta + kPartTile;                                   // regions
+    unsigned int* s_start = s_fill + t.regions;                                  // regions
+    unsigned int* s_gbase = s_start + t.regions;                                 // regions
+    __shared__ unsigned int scratch[33];
+    const int R = (int)t.regions;
+    unsigned int st = 0;
+    for (long long t0 = (long long)blockIdx.x * kPartTile; t0 < n; t0 += (long long)gridDim.x * kPartTile) {
+        for (int r = threadIdx.x; r < R; r += kBlock) s_fill[r] = 0u;
+        __syncthreads();
+        double2 p[kPartPer];
+#pragma unroll
+        for (int k = 0; k < kPartPer; ++k) {
+            const long long idx = t0 + k * kBlock + threadIdx.x;
+            if (idx < n) p[k] = __ldcs(xy + idx);
+        }
+#pragma unroll
+        for (int k = 0; k < kPartPer; ++k) {
+            const int j = k * kBlock + threadIdx.x;
+            const long long idx = t0 + j;
+            unsigned int meta = 0xFFFFFFFFu;
+            if (idx < n) {
+                const unsigned long long key = project_point<WIDE>(p[k].x, p[k].y, pp);
+                if (key == kInvalidKey) {
+                    st |= kStRange;
+                } else {
+                    const unsigned int r = region_of(key, t);
+                    meta = (r << 12) | atomicAdd(&s_fill[r], 1u);
+                    s_keys[j] = key;
+                }
+            }
+            s_meta[j] = meta;
+        }
+        __syncthreads();
+        const unsigned int total = block_excl_scan_bins(s_fill, R, s_start, scratch);
+        for (int r = threadIdx.x; r < R; r += kBlock)
+            if (s_fill[r]) s_gbase[r] = atomicAdd(&cursor[r], s_fill[r]);
+#pragma unroll
+        for (int k = 0; k < kPartPer; ++k) {
+            const int j = k * kBlock + threadIdx.x;
+            const unsigned int meta = s_meta[j];
+            if (meta != 0xFFFFFFFFu) s_sorted[s_start[meta >> 12] + (meta & 0xFFFu)] = s_keys[j];
+        }
+        __syncthreads();
+        for (unsigned int j0 = 0; j0 < total; j0 += kBlock) {  // block-uniform loop (warp ballots inside)
+            const unsigned int j = j0 + threadIdx.x;
+            unsigned long long key = 0;
+            bool spill = false;
+            if (j < total) {
+                key = s_sorted[j];
+                const unsigned int r = region_of(key, t);
+                const unsigned long long pos = (unsigned long long)s_gbase[r] + (j - s_start[r]);
+                if (pos < seg_cap)
+                    stage[(unsigned long long)r * seg_cap + pos] = key;
+                else
+                    spill = true;  // region far above its share: to the overflow list
+            }
+            overflow_append(spill, key, 1u, ovf_key, ovf_cnt, ovf_n);
+        }
+        __syncthreads();
+    }
+    if (st) atomicOr(d_status, st);
+}
+
+// Work items of pass 2: kInsertItem staged keys of one region; items are
+// numbered region after region.
+__global__ void __launch_bounds__(kBlock) k_region_items(const unsigned int* __restrict__ cursor, int regions,
+                                                        unsigned long long seg_cap, long long* item_start) {
+    __shared__ unsigned int scratch[33];
+    long long carry = 0;
+    for (int r0 = 0; r0 < regions; r0 += kBlock) {
+        const int r = r0 + threadIdx.x;
+        unsigned int items = 0;
+        if (r < regions) {
+            const unsigned long long c = min((unsigned long long)cursor[r], seg_cap);
+            items = (unsigned int)((c + kInsertItem - 1) / kInsertItem);
+        }
+        unsigned int tot;
+        const unsigned int off = block_excl_scan(items, scratch, &tot);
+        if (r < regions) item_start[r] = carry + off;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) item_start[regions] = carry;
+}
+
+__device__ __forceinline__ int find_region(const long long* __restrict__ start, int count, long long c) {
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= c)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Pass 2 of contraction: insert the staged keys, region after region, so the
+// table lines being updated stay in L2.  Equal keys within a warp are merged.
+// New tiles are only created while the table holds fewer than `new_limit`
+// tiles; past it, and for probe sequences longer than the bound, keys go to
+// the overflow list with their counts.  Table plus list always hold the exact
+// counts; the host grows the table and re-inserts the list.
+__global__ void __launch_bounds__(kBlock) k_insert(RegionTable t, const unsigned long long* __restrict__ stage,
+                                                  unsigned long long seg_cap, const unsigned int* __restrict__ cursor,
+                                                  const long long* __restrict__ item_start, int regions,
+                                                  unsigned long long new_limit, unsigned long long* d_newkeys,
+                                                  unsigned long long* ovf_key, unsigned int* ovf_cnt,
+                                                  unsigned long long* ovf_n) {
+    __shared__ int s_allow;
+    __shared__ unsigned int s_new;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long total = item_start[regions];
+    for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+        if (threadIdx.x == 0) {
+            s_allow = *reinterpret_cast<volatile unsigned long long*>(d_newkeys) < new_limit;
+            s_new = 0u;
+        }
+        __syncthreads();
+        const bool allow = s_allow != 0;
+        const int r = find_region(item_start, regions, it);
+        const unsigned long long cnt = min((unsigned long long)cursor[r], seg_cap);
+        const unsigned long long k0 = (unsigned long long)(it - item_start[r]) * kInsertItem;
+        const unsigned long long k1 = min(k0 + kInsertItem, cnt);
+        const unsigned long long* seg = stage + (unsigned long long)r * seg_cap;
+        unsigned int newk = 0;
+        for (unsigned long long base = k0 + warp * 32; base < k0 + kInsertItem; base += kBlock) {
+            const unsigned long long k = base + lane;
+            const unsigned long long key = k < k1 ? __ldcs(seg + k) : kInvalidKey;
+            const unsigned int grp = __match_any_sync(0xFFFFFFFFu, key);
+            const unsigned int c = (unsigned int)__popc(grp);
+            bool spill = false;
+            if (lane == __ffs(grp) - 1 && key != kInvalidKey) {
+                // past the new-tile limit the table is due to grow: spill at once
+                const int rc = allow ? rt_add(t, key, c) : -1;
+                if (rc > 0)
+                    ++newk;
+                else if (rc < 0)
+                    spill = true;
+            }
+            overflow_append(spill, key, c, ovf_key, ovf_cnt, ovf_n);
+        }
+        newk = __reduce_add_sync(0xFFFFFFFFu, newk);
+        if (lane == 0 && newk) atomicAdd(&s_new, newk);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_new) atomicAdd(d_newkeys, (unsigned long long)s_new);
+        __syncthreads();
+    }
+}
+
+// Re-insert the overflow list (after the table has grown); must succeed.
+__global__ void k_reinsert(RegionTable t, const unsigned long long* __restrict__ ovf_key,
+                           const unsigned int* __restrict__ ovf_cnt, unsigned long long n,
+                           unsigned long long* d_newkeys, unsigned int* d_status) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned int newk = 0, st = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int rc = rt_add(t, ovf_key[i], ovf_cnt[i]);
+        if (rc > 0)
+            ++newk;
+        else if (rc < 0)
+            st |= kStFull;
+    }
+    if (newk) atomicAdd(d_newkeys, (unsigned long long)newk);
+    if (st) atomicOr(d_status, st);
+}
+
+__global__ void k_rehash(const Slot* __restrict__ old_tab, unsigned long long old_cap, RegionTable t,
+                         unsigned int* d_status) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     unsigned int st = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < old_cap; i += stride) {
         const Slot s = old_tab[i];
-        if (s.key != kEmptyKey && table_add(tab, mask, s.key, s.count, max_probe) < 0) st |= kStFull;
+        if (s.key != kEmptyKey && rt_add(t, s.key, s.count) < 0) st |= kStFull;
     }
     if (st) atomicOr(d_status, st);
 }
@@ -170,8 +354,7 @@ __global__ void k_uf_init(const unsigned long long* d_nsig, int* parent, unsigne
 }
 
 __global__ void k_hook(const unsigned long long* d_nsig, const unsigned long long* __restrict__ sig_key,
-                       const Slot* __restrict__ tab, unsigned int mask, unsigned int max_probe, unsigned int tau,
-                       int* parent, unsigned int* d_status) {
+                       RegionTable t, unsigned int tau, int* parent, unsigned int* d_status) {
     const long long S = (long long)*d_nsig;
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned int st = 0;
@@ -180,8 +363,7 @@ __global__ void k_hook(const unsigned long long* d_nsig, const unsigned long lon
         const long long x = key_x(key), y = key_y(key);
         // forward neighbours: (x+1, y-1), (x+1, y), (x+1, y+1), (x, y+1); their
         // first probes are issued together
-        unsigned long long nk[4];
-        unsigned int ns[4];
+        unsigned long long nk[4], ns[4];
         Slot sl[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -189,14 +371,16 @@ __global__ void k_hook(const unsigned long long* d_nsig, const unsigned long lon
             const long long ny = y + (q < 3 ? q - 1 : 1);
             const bool valid = !(nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll);
             nk[q] = valid ? pack_key((int)nx, (int)ny) : kInvalidKey;
-            ns[q] = tile_hash(nk[q]) & mask;
-            if (valid) sl[q] = load_slot(&tab[ns[q]]);
-            else sl[q].key = kEmptyKey;
+            ns[q] = valid ? home_slot(nk[q], t) : 0ull;
+            if (valid)
+                sl[q] = load_slot(&t.tab[ns[q]]);
+            else
+                sl[q].key = kEmptyKey;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (nk[q] == kInvalidKey) continue;
-            const Slot nb = table_find_from(tab, mask, nk[q], ns[q], sl[q], max_probe);
+            const Slot nb = rt_lookup(t, nk[q], ns[q], sl[q]);
             if (nb.key != nk[q] || nb.count < tau) continue;
             if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
         }
@@ -269,8 +453,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsi
 }
 
 template <bool WIDE>
-__global__ void k_labels(const double2* __restrict__ xy, long long n, ProjParams pp, const Slot* __restrict__ tab,
-                         unsigned int mask, unsigned int max_probe, unsigned int tau,
+__global__ void k_labels(const double2* __restrict__ xy, long long n, ProjParams pp, RegionTable t, unsigned int tau,
                          const long long* __restrict__ cid_rows, long long* __restrict__ labels,
                          unsigned int* d_status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -282,11 +465,8 @@ __global__ void k_labels(const double2* __restrict__ xy, long long n, ProjParams
         if (key == kInvalidKey) {
             st |= kStRange;
         } else {
-            const long long s = table_find(tab, mask, key, max_probe);
-            if (s >= 0) {
-                const Slot sl = tab[s];
-                if (sl.count >= tau) lab = label_decode(key, sl.aux, cid_rows);
-            }
+            const Slot sl = rt_get(t, key);
+            if (sl.key == key && sl.count >= tau) lab = label_decode(key, sl.aux, cid_rows);
         }
         __stcs(labels + i, lab);
     }
@@ -326,15 +506,16 @@ struct raster_handle {
     enum { kContracting, kAgglomerated } state = kContracting;
 
     Slot* tab = nullptr;
-    unsigned long long cap = 0;  // power of two
+    unsigned long long cap = 0;  // regions << region_bits
+    unsigned int regions = 1, region_bits = 12;
     long long d_bound = 0;       // upper bound on distinct tiles
     long long points = 0;        // points submitted (incl. invalid ones)
 
-    // device counters: [0] new keys (D), [1] significant (S), [2] kept rows,
-    // [3] clusters, [4] export rows
+    // device counters: [0] tiles in the table (D), [1] significant (S),
+    // [2] kept rows, [3] clusters, [4] export rows, [5] overflow entries
     unsigned long long* d_ctr = nullptr;
     unsigned int* d_status = nullptr;
-    unsigned long long* h_ctr = nullptr;  // pinned mirror (5 counters + status)
+    unsigned long long* h_ctr = nullptr;  // pinned mirror: 6 counters, then the status word
 
     // agglomeration scratch and results (capacity in rows)
     long long agg_cap = 0;
@@ -348,6 +529,16 @@ struct raster_handle {
     unsigned int* out_cnt = nullptr;
     unsigned long long* out_cid = nullptr;
     raster_clusters result{};
+
+    // contraction staging: per-region key segments and cursors
+    unsigned long long* stage_keys = nullptr;
+    unsigned long long stage_cap = 0;  // keys
+    unsigned int* cursor = nullptr;
+    long long* item_start = nullptr;
+    unsigned int cursor_cap = 0;       // regions
+    unsigned long long* ovf_key = nullptr;
+    unsigned int* ovf_cnt = nullptr;
+    unsigned long long ovf_cap = 0;    // entries (one per point of a round)
 
     // host staging (contract_host / labels_host)
     cudaStream_t copy_stream = nullptr;
@@ -394,6 +585,32 @@ unsigned int max_probe_for(unsigned long long cap) {
     return (unsigned int)std::min<unsigned long long>(cap, 1ull << 22);
 }
 
+RegionTable table_of(const raster_handle* h) {
+    RegionTable t;
+    t.tab = h->tab;
+    t.cap = h->cap;
+    t.regions = h->regions;
+    t.region_bits = h->region_bits;
+    t.max_probe = max_probe_for(h->cap);
+    return t;
+}
+
+constexpr unsigned int kRegionBits = 20;  // 1M slots (16 MiB) per region
+
+// Table geometry for at least `need` slots: one power-of-two region up to
+// 2^kRegionBits slots, otherwise a whole number of 2^kRegionBits-slot regions.
+void geometry_for(double need, unsigned int* regions, unsigned int* bits) {
+    if (need <= (double)(1ull << kRegionBits)) {
+        unsigned int b = 12;
+        while ((double)(1ull << b) < need) ++b;
+        *regions = 1;
+        *bits = b;
+    } else {
+        *regions = (unsigned int)std::ceil(need / (double)(1ull << kRegionBits));
+        *bits = kRegionBits;
+    }
+}
+
 int fill_table(raster_handle* h, Slot* tab, unsigned long long cap, cudaStream_t s) {
     static int grid = grid_for((const void*)k_fill_table, kBlock);
     k_fill_table<<<grid, kBlock, 0, s>>>(tab, cap);
@@ -404,15 +621,17 @@ int fill_table(raster_handle* h, Slot* tab, unsigned long long cap, cudaStream_t
 
 // Read the device counters and status into h_ctr (synchronises the stream).
 int read_counters(raster_handle* h) {
-    RCHECK(h, cudaMemcpyAsync(h->h_ctr, h->d_ctr, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
-    RCHECK(h, cudaMemcpyAsync(h->h_ctr + 5, h->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+    RCHECK(h, cudaMemcpyAsync(h->h_ctr, h->d_ctr, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    h->h_ctr[6] = 0;
+    RCHECK(h, cudaMemcpyAsync(h->h_ctr + 6, h->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
     RCHECK(h, cudaStreamSynchronize(h->stream));
-    merge_status(h, status_from_bits((unsigned int)h->h_ctr[5]));
+    merge_status(h, status_from_bits((unsigned int)h->h_ctr[6]));
     return RASTER_OK;
 }
 
-// Replace the table by one of capacity new_cap, re-inserting every tile.
-int grow_table(raster_handle* h, unsigned long long new_cap) {
+// Replace the table by one of `regions` x 2^bits slots, re-inserting every tile.
+int grow_table(raster_handle* h, unsigned int regions, unsigned int bits) {
+    const unsigned long long new_cap = (unsigned long long)regions << bits;
     Slot* nt = nullptr;
     RCHECK(h, cudaMalloc(&nt, new_cap * sizeof(Slot)));
     int rc = fill_table(h, nt, new_cap, h->stream);
@@ -420,10 +639,15 @@ int grow_table(raster_handle* h, unsigned long long new_cap) {
         cudaFree(nt);
         return rc;
     }
+    RegionTable t;
+    t.tab = nt;
+    t.cap = new_cap;
+    t.regions = regions;
+    t.region_bits = bits;
+    t.max_probe = max_probe_for(new_cap);
     if (h->tab && h->cap) {
         static int grid = grid_for((const void*)k_rehash, kBlock);
-        k_rehash<<<grid, kBlock, 0, h->stream>>>(h->tab, h->cap, nt, (unsigned int)(new_cap - 1),
-                                                 max_probe_for(new_cap), h->d_status);
+        k_rehash<<<grid, kBlock, 0, h->stream>>>(h->tab, h->cap, t, h->d_status);
         note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -435,63 +659,133 @@ int grow_table(raster_handle* h, unsigned long long new_cap) {
     if (h->tab) cudaFree(h->tab);
     h->tab = nt;
     h->cap = new_cap;
+    h->regions = regions;
+    h->region_bits = bits;
     return RASTER_OK;
 }
 
-unsigned long long pow2_at_least(double v) {
-    unsigned long long c = 1ull << 12;
-    while ((double)c < v) c <<= 1;
-    return c;
+size_t part_smem(unsigned int regions) {
+    return (size_t)kPartTile * (8 + 8 + 4) + (size_t)regions * 12;
 }
 
-int ensure_room(raster_handle* h, long long want, long long* room_out) {
-    long long room = (long long)((double)h->cap * kMaxLoad) - h->d_bound;
-    if (room >= std::min(want, kMinStep) && room > 0) {
-        *room_out = room;
-        return RASTER_OK;
+int ensure_staging(raster_handle* h, long long n) {
+    const unsigned long long seg = (unsigned long long)std::ceil((double)n / h->regions * 1.25) + 2 * kPartTile;
+    const unsigned long long need = seg * h->regions;
+    if (need > h->stage_cap) {
+        RCHECK(h, cudaStreamSynchronize(h->stream));
+        if (h->stage_keys) cudaFree(h->stage_keys);
+        h->stage_keys = nullptr;
+        h->stage_cap = 0;
+        const unsigned long long cap = need + need / 8;
+        RCHECK(h, cudaMalloc(&h->stage_keys, cap * sizeof(unsigned long long)));
+        h->stage_cap = cap;
     }
-    int rc = read_counters(h);
-    if (rc) return rc;
-    h->d_bound = (long long)h->h_ctr[0];
-    room = (long long)((double)h->cap * kMaxLoad) - h->d_bound;
-    if (room < std::min(want, kMinStep) || room <= 0) {
-        const double need = (double)(h->d_bound + std::min(want, kGrowStep)) / kGrowLoad;
-        const unsigned long long nc = std::max(pow2_at_least(need), 2 * h->cap);
-        if (nc > (1ull << 31)) return RASTER_E_OOM;  // 32-bit slot indices
-        rc = grow_table(h, nc);
-        if (rc) return rc;
-        room = (long long)((double)h->cap * kMaxLoad) - h->d_bound;
+    if ((unsigned long long)n > h->ovf_cap) {
+        RCHECK(h, cudaStreamSynchronize(h->stream));
+        if (h->ovf_key) cudaFree(h->ovf_key);
+        if (h->ovf_cnt) cudaFree(h->ovf_cnt);
+        h->ovf_key = nullptr;
+        h->ovf_cnt = nullptr;
+        h->ovf_cap = 0;
+        RCHECK(h, cudaMalloc(&h->ovf_key, sizeof(unsigned long long) * (size_t)n));
+        RCHECK(h, cudaMalloc(&h->ovf_cnt, sizeof(unsigned int) * (size_t)n));
+        h->ovf_cap = (unsigned long long)n;
     }
-    *room_out = room;
+    if (h->regions > h->cursor_cap) {
+        RCHECK(h, cudaStreamSynchronize(h->stream));
+        if (h->cursor) cudaFree(h->cursor);
+        if (h->item_start) cudaFree(h->item_start);
+        h->cursor = nullptr;
+        h->item_start = nullptr;
+        h->cursor_cap = 0;
+        RCHECK(h, cudaMalloc(&h->cursor, sizeof(unsigned int) * h->regions));
+        RCHECK(h, cudaMalloc(&h->item_start, sizeof(long long) * (h->regions + 1)));
+        h->cursor_cap = h->regions;
+    }
     return RASTER_OK;
 }
 
+constexpr long long kRoundPoints = 256ll << 20;  // points per contraction round
+constexpr double kNewLimit = 0.8;                // no new tiles beyond this load within a round
+constexpr unsigned int kInsertProbe = 1024;      // longer probe sequences go to the overflow list
+
+// One contraction round of n points: pass 1, item prefix, pass 2 (all
+// asynchronous), then one synchronisation to read the table's tile count and
+// the overflow count.  If keys overflowed or the table is too full, grow it
+// and re-insert the overflow list.
 template <bool WIDE>
-void launch_contract(raster_handle* h, const double* xy, long long n) {
-    static int grid = grid_for((const void*)k_contract<WIDE, kContractUnroll>, kBlock);
-    const long long per_block = (long long)kBlock * kContractUnroll;
-    const long long need = (n + per_block - 1) / per_block;
-    const int g = (int)std::max<long long>(1, std::min<long long>(grid, need));
-    k_contract<WIDE, kContractUnroll><<<g, kBlock, 0, h->stream>>>(
-        reinterpret_cast<const double2*>(xy), n, h->pp, h->tab, (unsigned int)(h->cap - 1), max_probe_for(h->cap),
-        h->d_ctr, h->d_status);
-    note_launch();
+int contract_round(raster_handle* h, const double* xy, long long n) {
+    int rc = ensure_staging(h, n);
+    if (rc) return rc;
+    const unsigned long long seg = h->stage_cap / h->regions;
+    RegionTable t = table_of(h);
+    const size_t smem = part_smem(h->regions);
+    static bool attr_set = false;
+    if (!attr_set) {
+        RCHECK(h, cudaFuncSetAttribute(k_part<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set = true;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_part<WIDE>, kBlock, smem);
+    const long long tiles = (n + kPartTile - 1) / kPartTile;
+    const int g1 = (int)std::max<long long>(1, std::min<long long>((long long)sms * std::max(per_sm, 1), tiles));
+    RCHECK(h, cudaMemsetAsync(h->cursor, 0, sizeof(unsigned int) * h->regions, h->stream));
+    RCHECK(h, cudaMemsetAsync(h->d_ctr + 5, 0, sizeof(unsigned long long), h->stream));
+    k_part<WIDE><<<g1, kBlock, smem, h->stream>>>(reinterpret_cast<const double2*>(xy), n, h->pp, t, h->stage_keys,
+                                                 seg, h->cursor, h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_status);
+    k_region_items<<<1, kBlock, 0, h->stream>>>(h->cursor, (int)h->regions, seg, h->item_start);
+    static int g2 = grid_for((const void*)k_insert, kBlock);
+    RegionTable ti = t;
+    ti.max_probe = std::min<unsigned int>(t.max_probe, kInsertProbe);
+    k_insert<<<g2, kBlock, 0, h->stream>>>(ti, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
+                                          (unsigned long long)((double)h->cap * kNewLimit), h->d_ctr, h->ovf_key,
+                                          h->ovf_cnt, h->d_ctr + 5);
+    note_launch(3);
+    RCHECK(h, cudaGetLastError());
+    rc = read_counters(h);
+    if (rc) return rc;
+    const unsigned long long D = h->h_ctr[0], ovf = h->h_ctr[5];
+    bool grew = false;
+    if ((double)(D + ovf) > kMaxLoad * (double)h->cap) {  // D + ovf bounds the tile count
+        const double need = std::max((double)(D + ovf) / kGrowLoad, 1.5 * (double)h->cap);
+        unsigned int regions, bits;
+        geometry_for(need, &regions, &bits);
+        if (((unsigned long long)regions << bits) > (1ull << 32)) return RASTER_E_OOM;
+        rc = grow_table(h, regions, bits);
+        if (rc) return rc;
+        grew = true;
+    }
+    {
+        if (ovf > 0) {
+            static int g3 = grid_for((const void*)k_reinsert, kBlock);
+            k_reinsert<<<g3, kBlock, 0, h->stream>>>(table_of(h), h->ovf_key, h->ovf_cnt, ovf, h->d_ctr,
+                                                    h->d_status);
+            note_launch();
+            RCHECK(h, cudaGetLastError());
+            rc = read_counters(h);
+            if (rc) return rc;
+            // the growth estimate counted every overflowed point as a new tile;
+            // rebuild a table that ended up far larger than the tiles need
+            const double fit = (double)h->h_ctr[0] / kGrowLoad;
+            if (grew && (double)h->cap > 2.0 * fit && (double)h->cap > (double)(1ull << 20)) {
+                unsigned int regions, bits;
+                geometry_for(fit, &regions, &bits);
+                rc = grow_table(h, regions, bits);
+                if (rc) return rc;
+            }
+        }
+    }
+    h->d_bound = (long long)h->h_ctr[0];
+    return RASTER_OK;
 }
 
 int contract_device(raster_handle* h, const double* xy, long long n) {
-    long long off = 0;
-    while (off < n) {
-        long long room = 0;
-        int rc = ensure_room(h, n - off, &room);
+    for (long long off = 0; off < n; off += kRoundPoints) {
+        const long long m = std::min(n - off, kRoundPoints);
+        const int rc = h->wide ? contract_round<true>(h, xy + 2 * off, m) : contract_round<false>(h, xy + 2 * off, m);
         if (rc) return rc;
-        const long long m = std::min(n - off, room);
-        if (h->wide)
-            launch_contract<true>(h, xy + 2 * off, m);
-        else
-            launch_contract<false>(h, xy + 2 * off, m);
-        RCHECK(h, cudaGetLastError());
-        h->d_bound += m;
-        off += m;
     }
     return RASTER_OK;
 }
@@ -601,16 +895,16 @@ int raster_create(double precision, uint32_t tau, uint32_t mu, raster_handle** o
         delete h;
         return RASTER_E_ARG;
     }
-    cudaError_t e = cudaMalloc(&h->d_ctr, 5 * sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&h->d_ctr, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctr, 8 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, 5 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(unsigned int));
     if (e != cudaSuccess) {
         raster_destroy(h);
         return e == cudaErrorMemoryAllocation ? RASTER_E_OOM : RASTER_E_CUDA;
     }
-    int rc = grow_table(h, 1ull << 16);
+    int rc = grow_table(h, 1, 16);
     if (rc) {
         raster_destroy(h);
         return rc;
@@ -625,10 +919,12 @@ int raster_reserve(raster_handle* h, int64_t n_tiles) {
     int rc = read_counters(h);
     if (rc) return rc;
     h->d_bound = (long long)h->h_ctr[0];
-    const unsigned long long nc = pow2_at_least((double)std::max<long long>(n_tiles, h->d_bound) / kGrowLoad);
-    if (nc > (1ull << 31)) return RASTER_E_OOM;
-    if (nc <= h->cap) return RASTER_OK;
-    return grow_table(h, nc);
+    const double need = (double)std::max<long long>(n_tiles, h->d_bound) / kGrowLoad;
+    if (need <= (double)h->cap) return RASTER_OK;
+    unsigned int regions, bits;
+    geometry_for(need, &regions, &bits);
+    if (((unsigned long long)regions << bits) > (1ull << 32)) return RASTER_E_OOM;
+    return grow_table(h, regions, bits);
 }
 
 int raster_contract(raster_handle* h, const double* xy, int64_t n, void* stream) {
@@ -654,19 +950,30 @@ int raster_contract_host(raster_handle* h, const double* xy_host, int64_t n, voi
     h->points += n;
     RCHECK(h, cudaEventRecord(h->ev_done[0], h->stream));
     RCHECK(h, cudaEventRecord(h->ev_done[1], h->stream));
-    long long off = 0;
-    for (int c = 0; off < n; ++c) {
-        const int b = c & 1;
+    const long long nchunks = (n + h->stage_points - 1) / h->stage_points;
+    auto issue_copy = [&](long long c) -> int {
+        const int b = (int)(c & 1);
+        const long long off = c * h->stage_points;
         const long long m = std::min(n - off, h->stage_points);
         RCHECK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_done[b], 0));
         RCHECK(h, cudaMemcpyAsync(h->stage_xy[b], xy_host + 2 * off, (size_t)m * 16, cudaMemcpyHostToDevice,
                                   h->copy_stream));
         RCHECK(h, cudaEventRecord(h->ev_copied[b], h->copy_stream));
+        return RASTER_OK;
+    };
+    rc = issue_copy(0);
+    if (rc) return rc;
+    for (long long c = 0; c < nchunks; ++c) {
+        const int b = (int)(c & 1);
+        const long long m = std::min(n - c * h->stage_points, h->stage_points);
         RCHECK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
+        if (c + 1 < nchunks) {  // the next copy overlaps this chunk's contraction
+            rc = issue_copy(c + 1);
+            if (rc) return rc;
+        }
         rc = contract_device(h, h->stage_xy[b], m);
         if (rc) return rc;
         RCHECK(h, cudaEventRecord(h->ev_done[b], h->stream));
-        off += m;
     }
     RCHECK(h, cudaStreamSynchronize(h->stream));
     return RASTER_OK;
@@ -697,8 +1004,7 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     static int g_emit = grid_for((const void*)k_emit, kBlock);
     const int lim = (int)std::max<long long>(1, (D + kBlock - 1) / kBlock);
     k_uf_init<<<std::min(g_init, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->csize, h->cmin);
-    k_hook<<<std::min(g_hook, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->tab, (unsigned int)(h->cap - 1),
-                                                    max_probe_for(h->cap), h->tau, h->parent, h->d_status);
+    k_hook<<<std::min(g_hook, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->tau, h->parent, h->d_status);
     k_flatten<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent);
     k_stats<<<std::min(g_stat, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->parent, h->csize, h->cmin);
     k_emit<<<std::min(g_emit, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->sig_cnt, h->sig_slot, h->parent, h->csize,
@@ -731,15 +1037,13 @@ int raster_point_labels(raster_handle* h, const double* xy, int64_t n, int64_t* 
     if (h->wide) {
         static int grid = grid_for((const void*)k_labels<true>, kBlock);
         k_labels<true><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
-            reinterpret_cast<const double2*>(xy), n, h->pp, h->tab, (unsigned int)(h->cap - 1),
-            max_probe_for(h->cap), h->tau, reinterpret_cast<const long long*>(h->out_cid),
-            reinterpret_cast<long long*>(labels), h->d_status);
+            reinterpret_cast<const double2*>(xy), n, h->pp, table_of(h), h->tau,
+            reinterpret_cast<const long long*>(h->out_cid), reinterpret_cast<long long*>(labels), h->d_status);
     } else {
         static int grid = grid_for((const void*)k_labels<false>, kBlock);
         k_labels<false><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
-            reinterpret_cast<const double2*>(xy), n, h->pp, h->tab, (unsigned int)(h->cap - 1),
-            max_probe_for(h->cap), h->tau, reinterpret_cast<const long long*>(h->out_cid),
-            reinterpret_cast<long long*>(labels), h->d_status);
+            reinterpret_cast<const double2*>(xy), n, h->pp, table_of(h), h->tau,
+            reinterpret_cast<const long long*>(h->out_cid), reinterpret_cast<long long*>(labels), h->d_status);
     }
     note_launch();
     RCHECK(h, cudaGetLastError());
@@ -803,7 +1107,7 @@ int raster_reset(raster_handle* h, void* stream) {
     }
     int rc = fill_table(h, h->tab, h->cap, h->stream);
     if (rc) return rc;
-    RCHECK(h, cudaMemsetAsync(h->d_ctr, 0, 5 * sizeof(unsigned long long), h->stream));
+    RCHECK(h, cudaMemsetAsync(h->d_ctr, 0, 8 * sizeof(unsigned long long), h->stream));
     RCHECK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned int), h->stream));
     h->d_bound = 0;
     h->points = 0;
@@ -830,7 +1134,8 @@ int raster_destroy(raster_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* bufs[] = {h->tab,    h->d_ctr,   h->d_status, h->sig_key, h->sig_cnt, h->sig_slot, h->parent,
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
-                    h->stage_lab[0], h->stage_lab[1]};
+                    h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
+                    h->ovf_cnt};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);

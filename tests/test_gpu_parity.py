@@ -194,6 +194,26 @@ def test_table_growth_reserve_and_reset():
     assert_same(r2.agglomerate(), None, ref)
 
 
+def test_skewed_regions_spill_to_overflow_list():
+    """A table of many regions and points that all fall into one spatial block:
+    that region's staging segment overflows and the keys take the overflow
+    list; counts must still be exact."""
+    g = np.random.default_rng(9)
+    xy = np.concatenate([g.uniform(0.0, 0.16, size=(3_000_000, 2)),   # one 16 x 16 tile block
+                         g.uniform(0.0, 300.0, size=(200_000, 2))])
+    g.shuffle(xy)
+    ref, ref_lab, _ = oracle.raster(xy, 2, 5, 2, with_labels=True)
+    d = torch.from_numpy(xy).cuda()
+    r = R.Raster(2, 5, 2)
+    r.reserve(20_000_000)  # many regions
+    cap = r.capacity
+    for c in range(3):
+        r.contract(d[c * 1_066_667:(c + 1) * 1_066_667])
+    res = r.agglomerate()
+    assert r.capacity == cap  # spilling alone does not grow the table
+    assert_same(res, r.point_labels(d).cpu().numpy(), ref, ref_lab)
+
+
 def test_host_buffer_variants():
     w = gen.Workload(n=40_000_000, clusters=40_000, cluster_points=36_000_000, canvas=600.0, precision=2,
                      tau=5, mu=4, seed=88)
