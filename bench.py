@@ -65,6 +65,24 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over all ranks (timings: the job is as slow as its
+    slowest replica); the value itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, seconds: float) -> float:
+    """Weak scaling: every rank processes its own copy of the workload, so the
+    job processes world * units in the (max-over-ranks) time."""
+    return world * units_per_rank / seconds
+
+
 def workload_config(w: gen.Workload, name: str) -> dict:
     return {"workload": f"raster-{name}", "n_points": w.n, "clusters": w.clusters,
             "cluster_points": w.cluster_points, "canvas": [0.0, w.canvas], "precision": w.precision,
@@ -446,11 +464,7 @@ def run_gpu(args):
         dist.barrier()
     clocks = sampler.stop() if not args.profile else None
 
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
     phase = {"reset": [], "contract": [], "agglomerate": [], "labels": []}
     for (e0, e1, e2, e3, e4, res) in recs:
         phase["reset"].append(e0.elapsed_time(e1))
@@ -459,7 +473,7 @@ def run_gpu(args):
         phase["labels"].append(e3.elapsed_time(e4))
     res = recs[-1][5]
     ms_step = total_ms / args.steps
-    value = world * w.n / (ms_step / 1e3)
+    value = whole_job_rate(world, w.n, ms_step / 1e3)
 
     peaks = measured_peaks()
     contract_ms = statistics.mean(phase["contract"])
@@ -500,12 +514,8 @@ def run_gpu(args):
         for _ in range(n_e2e):
             e2e_step()
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / n_e2e
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        line["e2e"] = {"value": world * w.n / dt, "unit": "points/s", "h2d_bytes_per_step": POINT_BYTES * w.n,
+        dt = max_over_ranks((time.perf_counter() - t0) / n_e2e, dev)
+        line["e2e"] = {"value": whole_job_rate(world, w.n, dt), "unit": "points/s", "h2d_bytes_per_step": POINT_BYTES * w.n,
                        "d2h_bytes_per_step": 8 * w.n, "ms_per_step": dt * 1e3, "steps": n_e2e}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile:
