@@ -108,7 +108,7 @@ __device__ __forceinline__ void overflow_append(bool want, unsigned long long ke
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(kBlock) k_part(const double2* __restrict__ xy, long long n, ProjParams pp,
+__global__ void __launch_bounds__(kBlock, 4) k_part(const double2* __restrict__ xy, long long n, ProjParams pp,
                                                 RegionTable t, unsigned long long* __restrict__ stage,
                                                 unsigned long long seg_cap, unsigned int* __restrict__ cursor,
                                                 unsigned long long* ovf_key, unsigned int* ovf_cnt,
@@ -353,37 +353,27 @@ __global__ void k_uf_init(const unsigned long long* d_nsig, int* parent, unsigne
     }
 }
 
-__global__ void k_hook(const unsigned long long* d_nsig, const unsigned long long* __restrict__ sig_key,
-                       RegionTable t, unsigned int tau, int* parent, unsigned int* d_status) {
-    const long long S = (long long)*d_nsig;
+// One thread per (significant tile, forward neighbour): (x+1, y-1), (x+1, y),
+// (x+1, y+1), (x, y+1).  Adjacency at Chebyshev distance 1 is symmetric, so
+// these four directions visit every one of the eight neighbour pairs once; the
+// four lookups and unions of a tile run in parallel threads.
+__global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
+                                                const unsigned long long* __restrict__ sig_key, RegionTable t,
+                                                unsigned int tau, int* parent, unsigned int* d_status) {
+    const long long S4 = 4 * (long long)*d_nsig;
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned int st = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += stride) {
-        const unsigned long long key = __ldcs(sig_key + i);
-        const long long x = key_x(key), y = key_y(key);
-        // forward neighbours: (x+1, y-1), (x+1, y), (x+1, y+1), (x, y+1); their
-        // first probes are issued together
-        unsigned long long nk[4], ns[4];
-        Slot sl[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const long long nx = x + (q < 3 ? 1 : 0);
-            const long long ny = y + (q < 3 ? q - 1 : 1);
-            const bool valid = !(nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll);
-            nk[q] = valid ? pack_key((int)nx, (int)ny) : kInvalidKey;
-            ns[q] = valid ? home_slot(nk[q], t) : 0ull;
-            if (valid)
-                sl[q] = load_slot(&t.tab[ns[q]]);
-            else
-                sl[q].key = kEmptyKey;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (nk[q] == kInvalidKey) continue;
-            const Slot nb = rt_lookup(t, nk[q], ns[q], sl[q]);
-            if (nb.key != nk[q] || nb.count < tau) continue;
-            if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
-        }
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < S4; w += stride) {
+        const long long i = w >> 2;
+        const int q = (int)(w & 3);
+        const unsigned long long key = sig_key[i];
+        const long long nx = (long long)key_x(key) + (q < 3 ? 1 : 0);
+        const long long ny = (long long)key_y(key) + (q < 3 ? q - 1 : 1);
+        if (nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll) continue;
+        const unsigned long long nk = pack_key((int)nx, (int)ny);
+        const Slot nb = rt_get(t, nk);
+        if (nb.key != nk || nb.count < tau) continue;
+        if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
     }
     if (st) atomicOr(d_status, st);
 }
@@ -1004,7 +994,8 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     static int g_emit = grid_for((const void*)k_emit, kBlock);
     const int lim = (int)std::max<long long>(1, (D + kBlock - 1) / kBlock);
     k_uf_init<<<std::min(g_init, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->csize, h->cmin);
-    k_hook<<<std::min(g_hook, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->tau, h->parent, h->d_status);
+    k_hook<<<std::min<long long>(g_hook, 4ll * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->tau, h->parent,
+                                                                  h->d_status);
     k_flatten<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent);
     k_stats<<<std::min(g_stat, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->parent, h->csize, h->cmin);
     k_emit<<<std::min(g_emit, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->sig_cnt, h->sig_slot, h->parent, h->csize,
