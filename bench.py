@@ -38,6 +38,24 @@ import gen  # noqa: E402
 TILE_BYTES = 12          # algorithmic bytes per distinct tile (key + count written once)
 POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 
+# DRAM bytes (read + write) of one contraction phase -- k_part, k_region_items
+# and k_insert over both rounds -- in a steady-state step of the 500M-point
+# workload, from one ncu capture with one pass per launch
+# (profiles/raster_500m_dram_per_kernel.md).  Valid only for the kernel
+# sources it was measured with; reported as null otherwise.
+MEASURED_CONTRACT_TRAFFIC = {"sources": "9947e731cebf0796", "workload": "raster-500m", "bytes": 42_997_000_000}
+
+
+def kernel_sources_digest() -> str:
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1907_03620_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(csrc, "raster_single.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -432,7 +450,7 @@ def run_gpu(args):
         e1.record(stream)
         r.contract(xy)
         e2.record(stream)
-        res = r.agglomerate(copy=False)
+        res = r.agglomerate(copy=False, raw=True)
         e3.record(stream)
         r.point_labels(xy, out=labels)
         e4.record(stream)
@@ -479,10 +497,26 @@ def run_gpu(args):
     contract_ms = statistics.mean(phase["contract"])
     alg_bytes = POINT_BYTES * w.n + TILE_BYTES * res.n_distinct
     achieved = alg_bytes / (contract_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_contract (contraction phase)", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "peak_source": peaks["source"], "traffic": None,
-                "algorithmic_bytes": alg_bytes, "phase_ms": contract_ms}
+    traffic = None
+    if (not args.points and args.workload == "500m"
+            and kernel_sources_digest() == MEASURED_CONTRACT_TRAFFIC["sources"]):
+        traffic = MEASURED_CONTRACT_TRAFFIC["bytes"]
+    roofline = {"bound": "hbm", "kernel": "contraction phase: k_part + k_region_items + k_insert",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"] + " (copy bandwidth)",
+                "traffic": traffic, "traffic_unit": "bytes per contraction phase (ncu dram__bytes read+write)",
+                "algorithmic_bytes": alg_bytes, "algorithmic": "16 B/point + 12 B/distinct tile",
+                "phase_ms": contract_ms}
+    # the other phases of the step, against the same peak
+    ag_bytes = 12 * res.n_distinct + 24 * res.n_significant + 20 * int(res.key.numel())
+    lb_bytes = 24 * w.n
+    roofline_phases = {
+        "agglomerate": {"algorithmic_bytes": ag_bytes, "algorithmic": "12 B/tile + 24 B/significant + 20 B/kept row",
+                        "ms": statistics.mean(phase["agglomerate"]),
+                        "frac": ag_bytes / (statistics.mean(phase["agglomerate"]) / 1e3) / 1e9 / peaks["hbm_gbs"]},
+        "labels": {"algorithmic_bytes": lb_bytes, "algorithmic": "16 B/point read + 8 B/point written",
+                   "ms": statistics.mean(phase["labels"]),
+                   "frac": lb_bytes / (statistics.mean(phase["labels"]) / 1e3) / 1e9 / peaks["hbm_gbs"]}}
 
     line = {"metric": "points_per_s", "value": value, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -492,7 +526,8 @@ def run_gpu(args):
             "stats": {"n_distinct": res.n_distinct, "n_significant": res.n_significant,
                       "n_clusters": res.n_clusters, "kept_tiles": int(res.key.numel()),
                       "table_slots": r.capacity},
-            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+            "roofline": roofline, "roofline_phases": roofline_phases, "gpu_launches": int(launches),
+            "clocks": clocks}
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     if not args.no_e2e and not args.profile:
@@ -501,7 +536,7 @@ def run_gpu(args):
         def e2e_step():
             r.reset()
             r.contract_host(host)
-            res = r.agglomerate(copy=False)
+            res = r.agglomerate(copy=False, raw=True)
             r.point_labels_host(host, out=lab_host)
             return res
 

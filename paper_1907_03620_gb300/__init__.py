@@ -141,7 +141,10 @@ class Raster:
         check(self._L.raster_contract_host(self._h, ctypes.c_void_p(ptr), n, _stream_ptr(stream)),
               "raster_contract_host")
 
-    def agglomerate(self, copy: bool = True, allow_range_error: bool = False) -> Result:
+    def agglomerate(self, copy: bool = True, allow_range_error: bool = False, raw: bool = False) -> Result:
+        """copy=False returns views of the library's arrays; raw=True also keeps
+        the counts as the library's uint32 bits (an int32 view) so that no
+        torch kernel runs."""
         out = _native.Clusters()
         st = self._L.raster_agglomerate(self._h, ctypes.byref(out))
         if st != _native.OK and not (allow_range_error and st == _native.E_RANGE):
@@ -152,7 +155,8 @@ class Raster:
         cid = _view(out.cid, n, torch.int64, self.device)
         if copy:
             key, cid = key.clone(), cid.clone()
-        cnt = cnt.to(torch.int64) & 0xFFFFFFFF
+        if not raw:
+            cnt = cnt.to(torch.int64) & 0xFFFFFFFF
         return Result(key, cnt, cid, out.n_clusters, out.n_distinct, out.n_significant, out.n_points, st)
 
     def point_labels(self, xy: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -1,0 +1,74 @@
+"""The 500M-point workload in the bench's launch configuration (one handle,
+the whole array in one contract call), checked where the oracle can follow
+it: sampled tile counts are recomputed one by one over all points, sampled
+clusters are re-grown from the exported counts, sampled labels are checked,
+and the totals must hold."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_1907_03620_gb300 as R
+
+pytestmark = pytest.mark.gpu
+
+
+def _sorted_lookup(sorted_keys, values, q):
+    i = np.searchsorted(sorted_keys, q)
+    i = np.minimum(i, len(sorted_keys) - 1)
+    found = sorted_keys[i] == q
+    return found, np.where(found, values[i], 0)
+
+
+def test_workload_500m_sampled():
+    w = gen.C3_500M
+    xy = gen.points(w)
+    d = torch.from_numpy(xy).cuda()
+    r = R.Raster(w.precision, w.tau, w.mu)
+    r.contract(d)
+    res = r.agglomerate()
+    tk, tc = r.export_tiles()
+    lab = r.point_labels(d)
+    tk, tc = tk.cpu().numpy(), tc.cpu().numpy()
+    assert len(tk) == res.n_distinct and int(tc.sum()) == w.n
+    assert res.n_significant == int((tc >= w.tau).sum())
+    order = np.argsort(tk)
+    sk, sc = tk[order], tc[order]
+    rng = np.random.default_rng(17)
+    # 1. counts of sampled tiles (half of them significant) recomputed by the oracle over all points
+    sig = np.flatnonzero(tc >= w.tau)
+    sample = np.concatenate([tk[rng.choice(len(tk), 1000, replace=False)],
+                             tk[sig[rng.choice(len(sig), 1000, replace=False)]]])
+    want = oracle.count_keys(xy, oracle.scale_of(w.precision), sample)
+    _, got = _sorted_lookup(sk, sc, sample)
+    assert np.array_equal(got.astype(np.uint64), want)
+    # 2. sampled clusters re-grown over the exported counts (8-neighbour flood fill)
+    kk, kc = res.key.cpu().numpy(), res.cid.cpu().numpy()
+    korder = np.argsort(kk)
+    kks, kcs = kk[korder], kc[korder]
+    for cid in rng.choice(np.unique(kc), 60, replace=False):
+        members = set(kk[kc == cid].tolist())
+        start = int(cid)
+        seen, stack = {start}, [start]
+        while stack:
+            u = stack.pop()
+            x, y = int(np.int64(u) >> 32), int(np.int32(np.uint32(u & 0xFFFFFFFF)))
+            nb = np.array([int(oracle.pack(x + dx, y + dy)) for dx in (-1, 0, 1) for dy in (-1, 0, 1)
+                           if dx or dy], dtype=np.int64)
+            found, cnt = _sorted_lookup(sk, sc, nb)
+            for k, f, c in zip(nb.tolist(), found, cnt):
+                if f and c >= w.tau and k not in seen:
+                    seen.add(k)
+                    stack.append(k)
+        assert seen == members
+        assert len(members) >= w.mu
+        mx = min(members, key=lambda k: (np.int64(k) >> 32, np.int32(np.uint32(k & 0xFFFFFFFF))))
+        assert mx == cid
+    # 3. sampled labels: the point's tile (projected by the oracle) decides its label
+    idx = rng.choice(w.n, 20000, replace=False)
+    pk, ok = oracle.project(xy[idx], oracle.scale_of(w.precision))
+    assert ok.all()
+    found, cid = _sorted_lookup(kks, kcs, pk)
+    expect = np.where(found, cid, oracle.NOISE)
+    assert np.array_equal(lab[torch.from_numpy(idx).cuda()].cpu().numpy(), expect)
