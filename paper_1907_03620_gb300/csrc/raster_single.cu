@@ -71,7 +71,7 @@ __global__ void k_fill_table(Slot* tab, unsigned long long cap) {
 // share) go to the overflow list.
 constexpr int kPartTile = 2048;
 constexpr int kPartPer = kPartTile / kBlock;
-constexpr long long kInsertItem = 1024;
+constexpr long long kInsertItem = 2048;
 
 __device__ __forceinline__ unsigned int block_excl_scan_bins(unsigned int* bins, int nbins, unsigned int* start,
                                                              unsigned int* scratch) {
@@ -224,17 +224,23 @@ __global__ void __launch_bounds__(kBlock) k_insert(RegionTable t, const unsigned
                                                   const long long* __restrict__ item_start, int regions,
                                                   unsigned long long new_limit, unsigned long long* d_newkeys,
                                                   unsigned long long* ovf_key, unsigned int* ovf_cnt,
-                                                  unsigned long long* ovf_n) {
+                                                  unsigned long long* ovf_n, unsigned long long* work) {
     __shared__ int s_allow;
     __shared__ unsigned int s_new;
+    __shared__ long long s_it;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long total = item_start[regions];
-    for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    for (;;) {
+        // items are taken in order from a shared counter, so all blocks work on
+        // one narrow window of regions (a static stride lets blocks drift apart)
         if (threadIdx.x == 0) {
+            s_it = (long long)atomicAdd(work, 1ull);
             s_allow = *reinterpret_cast<volatile unsigned long long*>(d_newkeys) < new_limit;
             s_new = 0u;
         }
         __syncthreads();
+        const long long it = s_it;
+        if (it >= total) break;
         const bool allow = s_allow != 0;
         const int r = find_region(item_start, regions, it);
         const unsigned long long cnt = min((unsigned long long)cursor[r], seg_cap);
@@ -359,11 +365,21 @@ __global__ void k_uf_init(const unsigned long long* d_nsig, int* parent, unsigne
 // four lookups and unions of a tile run in parallel threads.
 __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
                                                 const unsigned long long* __restrict__ sig_key, RegionTable t,
-                                                unsigned int tau, int* parent, unsigned int* d_status) {
+                                                unsigned int tau, int* parent, unsigned long long* work,
+                                                unsigned int* d_status) {
+    __shared__ long long s_w0;
     const long long S4 = 4 * (long long)*d_nsig;
-    const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned int st = 0;
-    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < S4; w += stride) {
+    for (;;) {
+        // chunks of kBlock work items taken in order from a shared counter, so
+        // the rows in flight (and their table region) stay in one narrow window
+        if (threadIdx.x == 0) s_w0 = (long long)atomicAdd(work, 1ull) * kBlock;
+        __syncthreads();
+        const long long w0 = s_w0;  // read by all before thread 0 may overwrite it
+        __syncthreads();
+        if (w0 >= S4) break;
+        const long long w = w0 + threadIdx.x;
+        if (w >= S4) continue;
         const long long i = w >> 2;
         const int q = (int)(w & 3);
         const unsigned long long key = sig_key[i];
@@ -502,7 +518,8 @@ struct raster_handle {
     long long points = 0;        // points submitted (incl. invalid ones)
 
     // device counters: [0] tiles in the table (D), [1] significant (S),
-    // [2] kept rows, [3] clusters, [4] export rows, [5] overflow entries
+    // [2] kept rows, [3] clusters, [4] export rows, [5] overflow entries,
+    // [6] and [7] work counters of k_insert and k_hook
     unsigned long long* d_ctr = nullptr;
     unsigned int* d_status = nullptr;
     unsigned long long* h_ctr = nullptr;  // pinned mirror: 6 counters, then the status word
@@ -695,7 +712,7 @@ int ensure_staging(raster_handle* h, long long n) {
     return RASTER_OK;
 }
 
-constexpr long long kRoundPoints = 256ll << 20;  // points per contraction round
+constexpr long long kRoundPoints = 1ll << 30;    // points per contraction round
 constexpr double kNewLimit = 0.8;                // no new tiles beyond this load within a round
 constexpr unsigned int kInsertProbe = 1024;      // longer probe sequences go to the overflow list
 
@@ -729,9 +746,10 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
     static int g2 = grid_for((const void*)k_insert, kBlock);
     RegionTable ti = t;
     ti.max_probe = std::min<unsigned int>(t.max_probe, kInsertProbe);
+    RCHECK(h, cudaMemsetAsync(h->d_ctr + 6, 0, sizeof(unsigned long long), h->stream));
     k_insert<<<g2, kBlock, 0, h->stream>>>(ti, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
                                           (unsigned long long)((double)h->cap * kNewLimit), h->d_ctr, h->ovf_key,
-                                          h->ovf_cnt, h->d_ctr + 5);
+                                          h->ovf_cnt, h->d_ctr + 5, h->d_ctr + 6);
     note_launch(3);
     RCHECK(h, cudaGetLastError());
     rc = read_counters(h);
@@ -800,7 +818,7 @@ int ensure_agg_capacity(raster_handle* h, long long rows) {
 
 int ensure_stage(raster_handle* h) {
     if (h->stage_points) return RASTER_OK;
-    const long long pts = 16ll << 20;  // 16M points = 256 MiB of xy per buffer
+    const long long pts = 64ll << 20;  // 64M points = 1 GiB of xy per buffer
     RCHECK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
     for (int b = 0; b < 2; ++b) {
         RCHECK(h, cudaMalloc(&h->stage_xy[b], (size_t)pts * 16));
@@ -994,8 +1012,9 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     static int g_emit = grid_for((const void*)k_emit, kBlock);
     const int lim = (int)std::max<long long>(1, (D + kBlock - 1) / kBlock);
     k_uf_init<<<std::min(g_init, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->csize, h->cmin);
+    RCHECK(h, cudaMemsetAsync(h->d_ctr + 7, 0, sizeof(unsigned long long), s));
     k_hook<<<std::min<long long>(g_hook, 4ll * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->tau, h->parent,
-                                                                  h->d_status);
+                                                                  h->d_ctr + 7, h->d_status);
     k_flatten<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent);
     k_stats<<<std::min(g_stat, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->parent, h->csize, h->cmin);
     k_emit<<<std::min(g_emit, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->sig_cnt, h->sig_slot, h->parent, h->csize,
