@@ -359,6 +359,17 @@ __global__ void k_uf_init(const unsigned long long* d_nsig, int* parent, unsigne
     }
 }
 
+// Next chunk of kBlock rows for this block, taken in order from a shared
+// counter: rows in flight stay in one window (and so do the table regions and
+// union-find roots they touch).  Returns a value >= limit when done.
+__device__ __forceinline__ long long next_chunk(unsigned long long* work, long long* s_chunk) {
+    if (threadIdx.x == 0) *s_chunk = (long long)atomicAdd(work, 1ull) * kBlock;
+    __syncthreads();
+    const long long c = *s_chunk;
+    __syncthreads();
+    return c;
+}
+
 // One thread per (significant tile, forward neighbour): (x+1, y-1), (x+1, y),
 // (x+1, y+1), (x, y+1).  Adjacency at Chebyshev distance 1 is symmetric, so
 // these four directions visit every one of the eight neighbour pairs once; the
@@ -367,17 +378,10 @@ __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsi
                                                 const unsigned long long* __restrict__ sig_key, RegionTable t,
                                                 unsigned int tau, int* parent, unsigned long long* work,
                                                 unsigned int* d_status) {
-    __shared__ long long s_w0;
+    __shared__ long long s_chunk;
     const long long S4 = 4 * (long long)*d_nsig;
     unsigned int st = 0;
-    for (;;) {
-        // chunks of kBlock work items taken in order from a shared counter, so
-        // the rows in flight (and their table region) stay in one narrow window
-        if (threadIdx.x == 0) s_w0 = (long long)atomicAdd(work, 1ull) * kBlock;
-        __syncthreads();
-        const long long w0 = s_w0;  // read by all before thread 0 may overwrite it
-        __syncthreads();
-        if (w0 >= S4) break;
+    for (long long w0 = next_chunk(work, &s_chunk); w0 < S4; w0 = next_chunk(work, &s_chunk)) {
         const long long w = w0 + threadIdx.x;
         if (w >= S4) continue;
         const long long i = w >> 2;
@@ -394,21 +398,29 @@ __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsi
     if (st) atomicOr(d_status, st);
 }
 
-__global__ void k_flatten(const unsigned long long* d_nsig, int* parent) {
+__global__ void __launch_bounds__(kBlock) k_flatten(const unsigned long long* d_nsig, int* parent,
+                                                   unsigned long long* work) {
+    __shared__ long long s_chunk;
     const long long S = (long long)*d_nsig;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += stride)
-        parent[i] = uf_root(parent, (int)i);
+    for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
+        const long long i = c + threadIdx.x;
+        if (i < S) parent[i] = uf_root(parent, (int)i);
+    }
 }
 
-__global__ void k_stats(const unsigned long long* d_nsig, const unsigned long long* __restrict__ sig_key,
-                        const int* __restrict__ parent, unsigned int* csize, unsigned long long* cmin) {
+__global__ void __launch_bounds__(kBlock) k_stats(const unsigned long long* d_nsig,
+                                                 const unsigned long long* __restrict__ sig_key,
+                                                 const int* __restrict__ parent, unsigned int* csize,
+                                                 unsigned long long* cmin, unsigned long long* work) {
+    __shared__ long long s_chunk;
     const long long S = (long long)*d_nsig;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += stride) {
-        const int r = parent[i];
-        atomicAdd(&csize[r], 1u);
-        atomicMin(&cmin[r], order_of(sig_key[i]));
+    for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
+        const long long i = c + threadIdx.x;
+        if (i < S) {
+            const int r = parent[i];
+            atomicAdd(&csize[r], 1u);
+            atomicMin(&cmin[r], order_of(sig_key[i]));
+        }
     }
 }
 
@@ -420,12 +432,13 @@ __global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsi
                                                 const unsigned long long* __restrict__ cmin, unsigned int mu,
                                                 Slot* tab, unsigned long long* out_key, unsigned int* out_cnt,
                                                 unsigned long long* out_cid, unsigned long long* d_nkept,
-                                                unsigned long long* d_nclusters) {
+                                                unsigned long long* d_nclusters, unsigned long long* work) {
     __shared__ unsigned int scratch[33];
     __shared__ unsigned long long s_base;
+    __shared__ long long s_chunk;
     const long long S = (long long)*d_nsig;
     unsigned int clusters = 0;
-    for (long long t0 = (long long)blockIdx.x * kBlock; t0 < S; t0 += (long long)gridDim.x * kBlock) {
+    for (long long t0 = next_chunk(work, &s_chunk); t0 < S; t0 = next_chunk(work, &s_chunk)) {
         const long long i = t0 + threadIdx.x;
         bool keep = false;
         unsigned long long key = 0, cid = 0;
@@ -518,8 +531,7 @@ struct raster_handle {
     long long points = 0;        // points submitted (incl. invalid ones)
 
     // device counters: [0] tiles in the table (D), [1] significant (S),
-    // [2] kept rows, [3] clusters, [4] export rows, [5] overflow entries,
-    // [6] and [7] work counters of k_insert and k_hook
+    // [2] kept rows, [3] clusters, [4] export rows, [5] overflow entries
     unsigned long long* d_ctr = nullptr;
     unsigned int* d_status = nullptr;
     unsigned long long* h_ctr = nullptr;  // pinned mirror: 6 counters, then the status word
@@ -546,6 +558,8 @@ struct raster_handle {
     unsigned long long* ovf_key = nullptr;
     unsigned int* ovf_cnt = nullptr;
     unsigned long long ovf_cap = 0;    // entries (one per point of a round)
+
+    unsigned long long* d_work = nullptr;  // work counters of the ordered kernels (8)
 
     // host staging (contract_host / labels_host)
     cudaStream_t copy_stream = nullptr;
@@ -746,10 +760,10 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
     static int g2 = grid_for((const void*)k_insert, kBlock);
     RegionTable ti = t;
     ti.max_probe = std::min<unsigned int>(t.max_probe, kInsertProbe);
-    RCHECK(h, cudaMemsetAsync(h->d_ctr + 6, 0, sizeof(unsigned long long), h->stream));
+    RCHECK(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), h->stream));
     k_insert<<<g2, kBlock, 0, h->stream>>>(ti, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
                                           (unsigned long long)((double)h->cap * kNewLimit), h->d_ctr, h->ovf_key,
-                                          h->ovf_cnt, h->d_ctr + 5, h->d_ctr + 6);
+                                          h->ovf_cnt, h->d_ctr + 5, h->d_work);
     note_launch(3);
     RCHECK(h, cudaGetLastError());
     rc = read_counters(h);
@@ -904,6 +918,7 @@ int raster_create(double precision, uint32_t tau, uint32_t mu, raster_handle** o
         return RASTER_E_ARG;
     }
     cudaError_t e = cudaMalloc(&h->d_ctr, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_work, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctr, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, 8 * sizeof(unsigned long long));
@@ -1012,14 +1027,15 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     static int g_emit = grid_for((const void*)k_emit, kBlock);
     const int lim = (int)std::max<long long>(1, (D + kBlock - 1) / kBlock);
     k_uf_init<<<std::min(g_init, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->csize, h->cmin);
-    RCHECK(h, cudaMemsetAsync(h->d_ctr + 7, 0, sizeof(unsigned long long), s));
+    RCHECK(h, cudaMemsetAsync(h->d_work, 0, 8 * sizeof(unsigned long long), s));
     k_hook<<<std::min<long long>(g_hook, 4ll * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->tau, h->parent,
-                                                                  h->d_ctr + 7, h->d_status);
-    k_flatten<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent);
-    k_stats<<<std::min(g_stat, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->parent, h->csize, h->cmin);
+                                                                  h->d_work + 1, h->d_status);
+    k_flatten<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->d_work + 2);
+    k_stats<<<std::min(g_stat, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->parent, h->csize, h->cmin,
+                                                     h->d_work + 3);
     k_emit<<<std::min(g_emit, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->sig_cnt, h->sig_slot, h->parent, h->csize,
                                                     h->cmin, h->mu, h->tab, h->out_key, h->out_cnt, h->out_cid,
-                                                    h->d_ctr + 2, h->d_ctr + 3);
+                                                    h->d_ctr + 2, h->d_ctr + 3, h->d_work + 4);
     note_launch(5);
     RCHECK(h, cudaGetLastError());
     rc = read_counters(h);
@@ -1145,7 +1161,7 @@ int raster_destroy(raster_handle* h) {
     void* bufs[] = {h->tab,    h->d_ctr,   h->d_status, h->sig_key, h->sig_cnt, h->sig_slot, h->parent,
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
                     h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
-                    h->ovf_cnt};
+                    h->ovf_cnt, h->d_work};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
