@@ -39,11 +39,11 @@ TILE_BYTES = 12          # algorithmic bytes per distinct tile (key + count writ
 POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 
 # DRAM bytes (read + write) of one contraction phase -- k_part, k_region_items
-# and k_insert over both rounds -- in a steady-state step of the 500M-point
+# and k_insert -- in a steady-state step of the 500M-point
 # workload, from one ncu capture with one pass per launch
 # (profiles/raster_500m_dram_per_kernel.md).  Valid only for the kernel
 # sources it was measured with; reported as null otherwise.
-MEASURED_CONTRACT_TRAFFIC = {"sources": "9947e731cebf0796", "workload": "raster-500m", "bytes": 42_997_000_000}
+MEASURED_CONTRACT_TRAFFIC = {"sources": "66e01cd72cf372cc", "workload": "raster-500m", "bytes": 26_416_000_000}
 
 
 def kernel_sources_digest() -> str:
@@ -528,6 +528,27 @@ def run_gpu(args):
                       "table_slots": r.capacity},
             "roofline": roofline, "roofline_phases": roofline_phases, "gpu_launches": int(launches),
             "clocks": clocks}
+
+    # the same workload streamed as 10 chunks of 50M through raster_contract
+    # into one table (chunked processing): same step, chunked contraction
+    if not args.profile and w.n % 10 == 0:
+        m = w.n // 10
+        chunk_ms = []
+        for rep in range(3):
+            c0, c1 = ev(), ev()
+            c0.record(stream)
+            r.reset()
+            for c in range(10):
+                r.contract(xy[c * m:(c + 1) * m])
+            r.agglomerate(copy=False, raw=True)
+            r.point_labels(xy, out=labels)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                chunk_ms.append(c0.elapsed_time(c1))
+        cms = max_over_ranks(statistics.mean(chunk_ms), dev)
+        line["streamed_10_chunks"] = {"value": whole_job_rate(world, w.n, cms / 1e3), "unit": "points/s",
+                                      "ms_per_step": cms, "chunks": 10, "chunk_points": m}
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     if not args.no_e2e and not args.profile:

@@ -72,3 +72,15 @@ def test_workload_500m_sampled():
     found, cid = _sorted_lookup(kks, kcs, pk)
     expect = np.where(found, cid, oracle.NOISE)
     assert np.array_equal(lab[torch.from_numpy(idx).cuda()].cpu().numpy(), expect)
+    # 4. the same points streamed as 10 chunks of 50M into one table (Sect. 3.6) give the same table
+    r.close()
+    r2 = R.Raster(w.precision, w.tau, w.mu)
+    for c in range(10):
+        r2.contract(d[c * 50_000_000:(c + 1) * 50_000_000])
+    res2 = r2.agglomerate()
+    k2, c2 = r2.export_tiles()
+    k2, c2 = k2.cpu().numpy(), c2.cpu().numpy()
+    o2 = np.argsort(k2)
+    assert np.array_equal(k2[o2], sk) and np.array_equal(c2[o2], sc)
+    a, b = res.sorted(), res2.sorted()
+    assert torch.equal(a.key, b.key) and torch.equal(a.count, b.count) and torch.equal(a.cid, b.cid)
