@@ -43,7 +43,7 @@ POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 # workload, from one ncu capture with one pass per launch
 # (profiles/raster_500m_dram_per_kernel.md).  Valid only for the kernel
 # sources it was measured with; reported as null otherwise.
-MEASURED_CONTRACT_TRAFFIC = {"sources": "66e01cd72cf372cc", "workload": "raster-500m", "bytes": 26_416_000_000}
+MEASURED_CONTRACT_TRAFFIC = {"sources": "a965716eb866991d", "workload": "raster-500m", "bytes": 26_413_000_000}
 
 
 def kernel_sources_digest() -> str:
@@ -549,6 +549,31 @@ def run_gpu(args):
         cms = max_over_ranks(statistics.mean(chunk_ms), dev)
         line["streamed_10_chunks"] = {"value": whole_job_rate(world, w.n, cms / 1e3), "unit": "points/s",
                                       "ms_per_step": cms, "chunks": 10, "chunk_points": m}
+
+    # RASTER' grouped output (Sect. 3.4) on the same workload: the handle is
+    # agglomerated; point_groups re-projects every point and groups the
+    # indices of points in kept tiles by result row
+    if not args.profile:
+        res = r.agglomerate(copy=False, raw=True)
+        k = int(res.key.numel())
+        gbuf = (torch.empty(k + 1, dtype=torch.int64, device=dev), torch.empty(w.n, dtype=torch.int64, device=dev))
+        g_ms = []
+        for rep in range(4):
+            g0, g1 = ev(), ev()
+            g0.record(stream)
+            _, gidx = r.point_groups(xy, k, out=gbuf)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                g_ms.append(g0.elapsed_time(g1))
+        gms = max_over_ranks(statistics.mean(g_ms), dev)
+        g_bytes = POINT_BYTES * w.n + 8 * int(gidx.numel()) + 8 * (k + 1)
+        line["raster_prime_groups"] = {
+            "value": whole_job_rate(world, w.n, gms / 1e3), "unit": "points/s", "ms": gms,
+            "grouped_points": int(gidx.numel()), "rows": k, "algorithmic_bytes": g_bytes,
+            "algorithmic": "16 B/point read + 8 B/grouped point + 8 B/row written",
+            "frac": g_bytes / (gms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+        del gbuf, gidx
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     if not args.no_e2e and not args.profile:

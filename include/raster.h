@@ -118,6 +118,22 @@ int raster_point_labels(raster_handle *h, const double *xy, int64_t n, int64_t *
 int raster_point_labels_host(raster_handle *h, const double *xy_host, int64_t n, int64_t *labels_host,
                              void *stream);
 
+/* RASTER' output (Sect. 3.4; clusters as sets of points, Fig. 2d): the points
+ * of every kept tile, grouped by result row.  Requires a preceding
+ * raster_agglomerate with no contract since; rows follow the order of that
+ * call's raster_clusters.  For the n points at DEVICE xy (n x 2 float64,
+ * 16-byte aligned; normally the points that were contracted):
+ *   row_start   DEVICE int64[n_tiles + 1]: row r's points are
+ *               point_index[row_start[r] .. row_start[r+1]);
+ *   point_index DEVICE int64[capacity]: indices (0..n-1) of the points in
+ *               kept tiles, grouped by row; order within a row unspecified;
+ *   *n_grouped  HOST: number of such points (= row_start[n_tiles]).
+ * If capacity < *n_grouped nothing is written to point_index and
+ * RASTER_E_ARG is returned; the handle stays usable.  n above 2^32 - 1 is
+ * RASTER_E_LIMIT.  Synchronises `stream` once. */
+int raster_point_groups(raster_handle *h, const double *xy, int64_t n, int64_t *row_start, int64_t *point_index,
+                        int64_t capacity, int64_t *n_grouped, void *stream);
+
 /* The tile table after contraction (acc of Alg. 1): copy every tile with at
  * least one point (key, count) into caller DEVICE buffers of `capacity` rows;
  * *n_out receives D.  Order unspecified.

@@ -87,6 +87,8 @@ def _declare(L):
     L.oracle_labels.argtypes = [vp, vp, i64, vp]
     L.oracle_project.argtypes = [vp, i64, dbl, vp, vp]
     L.oracle_count_keys.argtypes = [vp, i64, dbl, vp, i64, vp]
+    L.oracle_point_groups.restype = i64
+    L.oracle_point_groups.argtypes = [vp, vp, i64, vp, vp, i64]
 
 
 def scale_of(precision: float) -> float:
@@ -149,6 +151,17 @@ class Oracle:
         cnt = np.empty(d, np.uint64)
         self.L.oracle_copy_tiles(self.h, key.ctypes.data, cnt.ctypes.data)
         return key, cnt
+
+    def point_groups(self, xy) -> tuple[np.ndarray, np.ndarray]:
+        """RASTER' (Sect. 3.4): (row_start, point_index) over the kept tiles in
+        the order of finish()'s rows, indices increasing within a row."""
+        a = _xy(xy)
+        k = self.L.oracle_n_kept(self.h)
+        row_start = np.empty(k + 1, np.int64)
+        idx = np.empty(max(a.shape[0], 1), np.int64)
+        m = self.L.oracle_point_groups(self.h, a.ctypes.data, a.shape[0], row_start.ctypes.data, idx.ctypes.data,
+                                       idx.shape[0])
+        return row_start, idx[:m]
 
     def labels(self, xy) -> tuple[int, np.ndarray]:
         a = _xy(xy)

@@ -251,6 +251,33 @@ int oracle_labels(const oracle_state *s, const double *xy, int64_t n, int64_t *l
     return st;
 }
 
+/* RASTER' output (Sect. 3.4): the points of every kept tile, rows in the
+ * order of oracle_copy_kept, indices increasing within a row.  row_start has
+ * n_kept + 1 entries; idx has room for `capacity` indices.  Returns the number
+ * of grouped points (idx untouched if it exceeds capacity). */
+int64_t oracle_point_groups(const oracle_state *s, const double *xy, int64_t n, int64_t *row_start, int64_t *idx,
+                            int64_t capacity) {
+    std::unordered_map<int64_t, int64_t> row_of;
+    for (size_t r = 0; r < s->kept_key.size(); ++r) row_of[s->kept_key[r]] = (int64_t)r;
+    std::vector<int64_t> rows(n, -1), count(s->kept_key.size(), 0);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t key;
+        if (!project(xy[2 * i], xy[2 * i + 1], s->scale, &key)) continue;
+        auto it = row_of.find(key);
+        if (it == row_of.end()) continue;
+        rows[i] = it->second;
+        count[it->second] += 1;
+    }
+    row_start[0] = 0;
+    for (size_t r = 0; r < count.size(); ++r) row_start[r + 1] = row_start[r] + count[r];
+    const int64_t m = row_start[count.size()];
+    if (m > capacity) return m;
+    std::vector<int64_t> cursor(row_start, row_start + count.size());
+    for (int64_t i = 0; i < n; ++i)
+        if (rows[i] >= 0) idx[cursor[rows[i]]++] = i;
+    return m;
+}
+
 /* Projection alone, for pinning: keys[i] and ok[i] (1 valid, 0 range error). */
 void oracle_project(const double *xy, int64_t n, double scale, int64_t *keys, uint8_t *ok) {
     for (int64_t i = 0; i < n; ++i) {

@@ -179,6 +179,25 @@ class Raster:
                                                _stream_ptr(stream)), "raster_point_labels_host")
         return out
 
+    def point_groups(self, xy: torch.Tensor, n_tiles: int, out=None, stream=None):
+        """RASTER' output: (row_start int64[n_tiles+1], point_index int64[m]) --
+        the indices of the points of each kept tile, rows in the order of the
+        last agglomerate() result (n_tiles = its number of rows).  `out` may
+        give (row_start, point_index) buffers of n_tiles+1 and n entries."""
+        _check_points(xy, "point_groups")
+        n = xy.shape[0]
+        if out is None:
+            out = (torch.empty(n_tiles + 1, dtype=torch.int64, device=xy.device),
+                   torch.empty(max(n, 1), dtype=torch.int64, device=xy.device))  # at most n grouped points
+        row_start, idx = out
+        for t, size in ((row_start, n_tiles + 1), (idx, n)):
+            assert t.is_cuda and t.dtype == torch.int64 and t.is_contiguous() and t.numel() >= size
+        m = ctypes.c_int64()
+        check(self._L.raster_point_groups(self._h, ctypes.c_void_p(xy.data_ptr()), n,
+                                          ctypes.c_void_p(row_start.data_ptr()), ctypes.c_void_p(idx.data_ptr()),
+                                          idx.numel(), ctypes.byref(m), _stream_ptr(stream)), "raster_point_groups")
+        return row_start[:n_tiles + 1], idx[:m.value]
+
     def export_tiles(self):
         """All tiles with at least one point: (key int64, count int64) CUDA tensors."""
         n = ctypes.c_int64()

@@ -80,6 +80,7 @@ def _declare(L):
         "raster_point_labels": (ci, [vp, vp, i64, vp, vp]),
         "raster_point_labels_host": (ci, [vp, vp, i64, vp, vp]),
         "raster_export_tiles": (ci, [vp, vp, vp, i64, ctypes.POINTER(i64)]),
+        "raster_point_groups": (ci, [vp, vp, i64, vp, vp, i64, ctypes.POINTER(i64), vp]),
         "raster_reset": (ci, [vp, vp]),
         "raster_status": (ci, [vp]),
         "raster_get_scale": (dbl, [vp]),

@@ -431,8 +431,9 @@ __global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsi
                                                 const int* __restrict__ parent, const unsigned int* __restrict__ csize,
                                                 const unsigned long long* __restrict__ cmin, unsigned int mu,
                                                 Slot* tab, unsigned long long* out_key, unsigned int* out_cnt,
-                                                unsigned long long* out_cid, unsigned long long* d_nkept,
-                                                unsigned long long* d_nclusters, unsigned long long* work) {
+                                                unsigned long long* out_cid, unsigned int* out_slot,
+                                                unsigned long long* d_nkept, unsigned long long* d_nclusters,
+                                                unsigned long long* work) {
     __shared__ unsigned int scratch[33];
     __shared__ unsigned long long s_base;
     __shared__ long long s_chunk;
@@ -461,6 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsi
                 out_key[row] = key;
                 out_cnt[row] = sig_cnt[i];
                 out_cid[row] = cid;
+                out_slot[row] = sig_slot[i];
                 code = label_code(key, cid, (unsigned int)row);
             }
             tab[sig_slot[i]].aux = code;
@@ -490,6 +492,121 @@ __global__ void k_labels(const double2* __restrict__ xy, long long n, ProjParams
         __stcs(labels + i, lab);
     }
     if (st) atomicOr(d_status, st);
+}
+
+// RASTER' (Sect. 3.4): the points of every kept tile, as a CSR over result
+// rows.  The slots of kept tiles temporarily hold their result row in aux.
+__global__ void k_aux_rows(const unsigned long long* d_nkept, const unsigned int* __restrict__ out_slot, Slot* tab) {
+    const long long K = (long long)*d_nkept;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < K; r += stride)
+        tab[out_slot[r]].aux = (unsigned int)r;
+}
+
+__global__ void k_aux_codes(const unsigned long long* d_nkept, const unsigned int* __restrict__ out_slot,
+                            const unsigned long long* __restrict__ out_key,
+                            const unsigned long long* __restrict__ out_cid, Slot* tab) {
+    const long long K = (long long)*d_nkept;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < K; r += stride)
+        tab[out_slot[r]].aux = label_code(out_key[r], out_cid[r], (unsigned int)r);
+}
+
+template <bool WIDE>
+__global__ void k_group_count(const double2* __restrict__ xy, long long n, ProjParams pp, RegionTable t,
+                              unsigned int tau, unsigned int* row_count, int* point_row, unsigned int* d_status) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned int st = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double2 p = __ldcs(xy + i);
+        const unsigned long long key = project_point<WIDE>(p.x, p.y, pp);
+        int row = -1;
+        if (key == kInvalidKey) {
+            st |= kStRange;
+        } else {
+            const Slot sl = rt_get(t, key);
+            if (sl.key == key && sl.count >= tau && sl.aux != kAuxNone) {
+                row = (int)sl.aux;
+                atomicAdd(&row_count[row], 1u);
+            }
+        }
+        point_row[i] = row;
+    }
+    if (st) atomicOr(d_status, st);
+}
+
+// Exclusive scan of row_count[0..K) into row_start[0..K]; three launches.
+constexpr int kScanTile = kBlock * 8;
+__global__ void __launch_bounds__(kBlock) k_scan_tiles(const unsigned long long* d_nkept,
+                                                      const unsigned int* __restrict__ in, long long* out,
+                                                      long long* tile_sums) {
+    __shared__ unsigned int scratch[33];
+    const long long K = (long long)*d_nkept;
+    for (long long t0 = (long long)blockIdx.x * kScanTile; t0 < K; t0 += (long long)gridDim.x * kScanTile) {
+        unsigned int v[8];
+        unsigned int sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const long long i = t0 + threadIdx.x * 8 + k;
+            v[k] = i < K ? in[i] : 0u;
+            sum += v[k];
+        }
+        unsigned int total;
+        unsigned int off = block_excl_scan(sum, scratch, &total);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const long long i = t0 + threadIdx.x * 8 + k;
+            if (i < K) out[i] = off;
+            off += v[k];
+        }
+        if (threadIdx.x == 0) tile_sums[t0 / kScanTile] = total;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_sums(const unsigned long long* d_nkept, long long* tile_sums,
+                                                     long long* out) {
+    __shared__ long long s_part[kBlock];
+    const long long K = (long long)*d_nkept;
+    const long long T = (K + kScanTile - 1) / kScanTile;
+    // each thread owns a contiguous run of tile sums
+    const long long per = (T + kBlock - 1) / kBlock;
+    const long long a = threadIdx.x * per, b = min(a + per, T);
+    long long sum = 0;
+    for (long long j = a; j < b; ++j) sum += tile_sums[j];
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int j = 0; j < kBlock; ++j) {
+            const long long x = s_part[j];
+            s_part[j] = acc;
+            acc += x;
+        }
+        out[K] = acc;  // total points in kept tiles
+    }
+    __syncthreads();
+    long long acc = s_part[threadIdx.x];
+    for (long long j = a; j < b; ++j) {
+        const long long x = tile_sums[j];
+        tile_sums[j] = acc;
+        acc += x;
+    }
+}
+
+__global__ void k_scan_add(const unsigned long long* d_nkept, const long long* __restrict__ tile_sums, long long* out) {
+    const long long K = (long long)*d_nkept;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride)
+        out[i] += tile_sums[i / kScanTile];
+}
+
+__global__ void k_group_scatter(long long n, const int* __restrict__ point_row, const long long* __restrict__ row_start,
+                                unsigned int* cursor, long long* point_index) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int r = point_row[i];
+        if (r >= 0) point_index[row_start[r] + atomicAdd(&cursor[r], 1u)] = i;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -547,7 +664,14 @@ struct raster_handle {
     unsigned long long* out_key = nullptr;
     unsigned int* out_cnt = nullptr;
     unsigned long long* out_cid = nullptr;
+    unsigned int* out_slot = nullptr;  // table slot of each result row
     raster_clusters result{};
+    // RASTER' point groups: row of each point, per-row counters
+    int* point_row = nullptr;
+    long long point_row_cap = 0;
+    unsigned int* row_count = nullptr;
+    long long* scan_sums = nullptr;
+    long long row_count_cap = 0;
 
     // contraction staging: per-region key segments and cursors
     unsigned long long* stage_keys = nullptr;
@@ -817,15 +941,15 @@ int ensure_agg_capacity(raster_handle* h, long long rows) {
     const long long cap = std::max<long long>(rows + rows / 4, 1 << 16);
     void** bufs[] = {(void**)&h->sig_key, (void**)&h->sig_cnt, (void**)&h->sig_slot, (void**)&h->parent,
                      (void**)&h->csize,   (void**)&h->cmin,    (void**)&h->out_key,  (void**)&h->out_cnt,
-                     (void**)&h->out_cid};
-    const size_t sizes[] = {8, 4, 4, 4, 4, 8, 8, 4, 8};
+                     (void**)&h->out_cid, (void**)&h->out_slot};
+    const size_t sizes[] = {8, 4, 4, 4, 4, 8, 8, 4, 8, 4};
     RCHECK(h, cudaStreamSynchronize(h->stream));
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < 10; ++i) {
         if (*bufs[i]) cudaFree(*bufs[i]);
         *bufs[i] = nullptr;
     }
     h->agg_cap = 0;
-    for (int i = 0; i < 9; ++i) RCHECK(h, cudaMalloc(bufs[i], (size_t)cap * sizes[i]));
+    for (int i = 0; i < 10; ++i) RCHECK(h, cudaMalloc(bufs[i], (size_t)cap * sizes[i]));
     h->agg_cap = cap;
     return RASTER_OK;
 }
@@ -1035,7 +1159,7 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
                                                      h->d_work + 3);
     k_emit<<<std::min(g_emit, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->sig_cnt, h->sig_slot, h->parent, h->csize,
                                                     h->cmin, h->mu, h->tab, h->out_key, h->out_cnt, h->out_cid,
-                                                    h->d_ctr + 2, h->d_ctr + 3, h->d_work + 4);
+                                                    h->out_slot, h->d_ctr + 2, h->d_ctr + 3, h->d_work + 4);
     note_launch(5);
     RCHECK(h, cudaGetLastError());
     rc = read_counters(h);
@@ -1107,6 +1231,76 @@ int raster_point_labels_host(raster_handle* h, const double* xy_host, int64_t n,
     return RASTER_OK;
 }
 
+int raster_point_groups(raster_handle* h, const double* xy, int64_t n, int64_t* row_start, int64_t* point_index,
+                        int64_t capacity, int64_t* n_grouped, void* stream) {
+    if (!h || n < 0 || !n_grouped || !row_start || capacity < 0 || (n > 0 && (!xy || misaligned(xy))))
+        return RASTER_E_ARG;
+    if (hard_error(h->status)) return h->status;
+    if (h->state != raster_handle::kAgglomerated) return RASTER_E_STATE;
+    if (n > 0xFFFFFFFFll) return RASTER_E_LIMIT;  // per-row counters are 32-bit
+    h->stream = (cudaStream_t)stream;
+    cudaStream_t s = h->stream;
+    const long long K = h->result.n_tiles;
+    // scratch: a row per point, a counter and a cursor per result row
+    if (n > h->point_row_cap) {
+        RCHECK(h, cudaStreamSynchronize(s));
+        if (h->point_row) cudaFree(h->point_row);
+        h->point_row = nullptr;
+        h->point_row_cap = 0;
+        RCHECK(h, cudaMalloc(&h->point_row, sizeof(int) * (size_t)std::max<long long>(n, 1)));
+        h->point_row_cap = std::max<long long>(n, 1);
+    }
+    if (K + 1 > h->row_count_cap) {
+        RCHECK(h, cudaStreamSynchronize(s));
+        if (h->row_count) cudaFree(h->row_count);
+        if (h->scan_sums) cudaFree(h->scan_sums);
+        h->row_count = nullptr;
+        h->scan_sums = nullptr;
+        h->row_count_cap = 0;
+        const long long cap = K + 1;
+        RCHECK(h, cudaMalloc(&h->row_count, sizeof(unsigned int) * (size_t)cap));
+        RCHECK(h, cudaMalloc(&h->scan_sums, sizeof(long long) * (size_t)(cap / kScanTile + 2)));
+        h->row_count_cap = cap;
+    }
+    const unsigned long long* d_nkept = h->d_ctr + 2;
+    static int g = grid_for((const void*)k_aux_rows, kBlock);
+    const int gk = (int)std::max<long long>(1, std::min<long long>(g, (K + kBlock - 1) / kBlock));
+    RCHECK(h, cudaMemsetAsync(h->row_count, 0, sizeof(unsigned int) * (size_t)(K + 1), s));
+    k_aux_rows<<<gk, kBlock, 0, s>>>(d_nkept, h->out_slot, h->tab);
+    if (n > 0) {
+        const int gp = (int)std::min<long long>(grid_for((const void*)k_group_count<false>, kBlock),
+                                                (n + kBlock - 1) / kBlock);
+        if (h->wide)
+            k_group_count<true><<<gp, kBlock, 0, s>>>(reinterpret_cast<const double2*>(xy), n, h->pp, table_of(h),
+                                                     h->tau, h->row_count, h->point_row, h->d_status);
+        else
+            k_group_count<false><<<gp, kBlock, 0, s>>>(reinterpret_cast<const double2*>(xy), n, h->pp, table_of(h),
+                                                      h->tau, h->row_count, h->point_row, h->d_status);
+    }
+    const int gs = (int)std::max<long long>(1, std::min<long long>(1024, (K + kScanTile - 1) / kScanTile));
+    long long* rs = reinterpret_cast<long long*>(row_start);
+    k_scan_tiles<<<gs, kBlock, 0, s>>>(d_nkept, h->row_count, rs, h->scan_sums);
+    k_scan_sums<<<1, kBlock, 0, s>>>(d_nkept, h->scan_sums, rs);
+    k_scan_add<<<gk, kBlock, 0, s>>>(d_nkept, h->scan_sums, rs);
+    k_aux_codes<<<gk, kBlock, 0, s>>>(d_nkept, h->out_slot, h->out_key, h->out_cid, h->tab);
+    note_launch(n > 0 ? 6 : 5);
+    RCHECK(h, cudaGetLastError());
+    long long m = 0;
+    RCHECK(h, cudaMemcpyAsync(&m, row_start + K, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    RCHECK(h, cudaStreamSynchronize(s));
+    *n_grouped = m;
+    if (m > capacity || (m > 0 && !point_index)) return RASTER_E_ARG;
+    if (m > 0) {
+        RCHECK(h, cudaMemsetAsync(h->row_count, 0, sizeof(unsigned int) * (size_t)K, s));  // reuse as cursors
+        static int g2 = grid_for((const void*)k_group_scatter, kBlock);
+        k_group_scatter<<<(int)std::min<long long>(g2, (n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+            n, h->point_row, rs, h->row_count, reinterpret_cast<long long*>(point_index));
+        note_launch();
+        RCHECK(h, cudaGetLastError());
+    }
+    return RASTER_OK;
+}
+
 int raster_export_tiles(raster_handle* h, int64_t* key, uint32_t* count, int64_t capacity, int64_t* n_out) {
     if (!h || !n_out || capacity < 0) return RASTER_E_ARG;
     if (hard_error(h->status)) return h->status;
@@ -1161,7 +1355,7 @@ int raster_destroy(raster_handle* h) {
     void* bufs[] = {h->tab,    h->d_ctr,   h->d_status, h->sig_key, h->sig_cnt, h->sig_slot, h->parent,
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
                     h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
-                    h->ovf_cnt, h->d_work};
+                    h->ovf_cnt, h->d_work, h->out_slot, h->point_row, h->row_count, h->scan_sums};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);

@@ -295,6 +295,25 @@ def test_labels_follow_kept_tiles():
     assert (lab != oracle.NOISE).sum() > 0
 
 
+def test_point_groups_raster_prime():
+    """RASTER' (Sect. 3.4) returns clusters as points: every grouped point lies
+    in its row's tile (numpy's floor decides), each row holds exactly that
+    tile's count, and the grouped points are exactly the labelled ones."""
+    w = gen.Workload(n=40_000, clusters=40, cluster_points=36_000, canvas=4.0, precision=2, tau=5, mu=4, seed=51)
+    xy = gen.points(w)
+    r, lab, o = oracle.raster(xy, 2, 5, 4, with_labels=True)
+    row_start, idx = o.point_groups(xy)
+    assert row_start[0] == 0 and len(row_start) == len(r.key) + 1
+    assert np.array_equal(np.diff(row_start), r.count.astype(np.int64))
+    f = np.floor(xy * 100.0).astype(np.int64)
+    pk = oracle.pack(f[:, 0], f[:, 1])
+    for row in range(len(r.key)):
+        members = idx[row_start[row]:row_start[row + 1]]
+        assert np.all(pk[members] == r.key[row])
+        assert np.all(np.diff(members) > 0)
+    assert np.array_equal(np.sort(idx), np.flatnonzero(lab != oracle.NOISE))
+
+
 def test_range_errors_are_reported_and_skipped():
     xy = np.array([[0.5, 0.5], [math.nan, 0.5], [0.5, math.inf], [3e7, 0.5], [0.51, 0.52]])
     o = oracle.Oracle(2, 1, 1)
