@@ -49,7 +49,7 @@ __device__ __forceinline__ bool project_coord(double v, const ProjParams& pp, in
     const unsigned long long mx = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
     unsigned long long q;
     if (!WIDE) {
-        const unsigned long long P = mx * pp.s_odd;  // < 2^63
+        const unsigned long long P = mx * (unsigned long long)(unsigned int)pp.s_odd;  // < 2^63 (s_odd < 2^10)
         const int D = pp.d0 - (int)e;                 // v*s = P * 2^-D
         if (D <= 0) return false;                     // |v*s| >= 2^52
         const int t = pp.top + (int)((P >> pp.top) != 0ull);  // bit length of P

@@ -2,15 +2,17 @@
 //
 // The table is split into `regions` regions of 2^region_bits slots.  A tile's
 // home slot is in the region chosen by a hash of its 16 x 16-tile spatial
-// block, at an offset chosen by a hash of the tile itself; probing is linear
-// over the whole table.  Two consequences shape the kernels:
+// block, at an offset chosen by a hash of the tile itself.  Each region is a
+// whole number of buckets of 2^kBucketBits slots (64 KiB), and probing is
+// linear within the home bucket, wrapping at its end.  Two consequences shape
+// the kernels:
 //   * the eight neighbours of a tile almost always share its region, so the
 //     agglomeration's neighbour probes (which walk significant tiles in slot
 //     order) and its union-find accesses stay within a few regions at a time
 //     and hit L2;
-//   * contraction can sort the keys of a chunk by region first and then
-//     insert region after region, so the table lines being updated are a
-//     small, L2-resident part of the table at any moment.
+//   * contraction sorts a round's keys by region and then by bucket, and
+//     inserts each bucket's keys into a copy of the bucket in shared memory,
+//     so the table is read and written once per round, in whole buckets.
 #pragma once
 
 #include "raster_device.cuh"
@@ -18,6 +20,8 @@
 namespace raster {
 
 constexpr int kBlockShift = 4;  // spatial blocks of 16 x 16 tiles
+constexpr int kBucketBits = 12;  // probing stays within 4096-slot buckets
+constexpr unsigned int kBucketSlots = 1u << kBucketBits;
 
 struct RegionTable {
     Slot* tab;
@@ -48,8 +52,8 @@ __device__ __forceinline__ unsigned long long home_slot(unsigned long long key, 
            (unsigned long long)(tile_hash(key) & ((1u << t.region_bits) - 1u));
 }
 
-__device__ __forceinline__ unsigned long long next_slot(unsigned long long i, const RegionTable& t) {
-    return (i + 1ull == t.cap) ? 0ull : i + 1ull;
+__device__ __forceinline__ unsigned long long next_slot(unsigned long long i, const RegionTable&) {
+    return (i & ~(unsigned long long)(kBucketSlots - 1u)) | ((i + 1ull) & (kBucketSlots - 1u));
 }
 
 // Add c points to `key`: 1 if new, 0 if present, -1 if max_probe slots failed.

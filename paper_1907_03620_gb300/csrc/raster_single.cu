@@ -64,8 +64,9 @@ __global__ void k_fill_table(Slot* tab, unsigned long long cap) {
         reinterpret_cast<ulonglong2*>(tab)[i] = v;
 }
 
-// Pass 1 of contraction: project a tile of kPartTile points, counting-sort the
-// keys by table region in shared memory, reserve space in each region's
+// Pass 1 of contraction: project a tile of kPartTile points (keys stay in
+// registers), counting-sort the keys by table region in shared memory (with
+// each key's region beside it, as a 16-bit index), reserve space in each region's
 // staging segment with one atomic per (tile, region), and append the keys in
 // coalesced runs.  Keys beyond a segment's capacity (a region far above its
 // share) go to the overflow list.
@@ -114,12 +115,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double2* __restrict__ 
                                                 unsigned long long* ovf_key, unsigned int* ovf_cnt,
                                                 unsigned long long* ovf_n, unsigned int* d_status) {
     extern __shared__ unsigned char smem[];
-    unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(smem);   // kPartTile
-    unsigned long long* s_sorted = s_keys + kPartTile;                           // kPartTile
-    unsigned int* s_meta = reinterpret_cast<unsigned int*>(s_sorted + kPartTile); // kPartTile
-    unsigned int* s_fill = s_meta + kPartTile;                                   // regions
-    unsigned int* s_start = s_fill + t.regions;                                  // regions
-    unsigned int* s_gbase = s_start + t.regions;                                 // regions
+    unsigned long long* s_sorted = reinterpret_cast<unsigned long long*>(smem);         // kPartTile keys
+    unsigned int* s_fill = reinterpret_cast<unsigned int*>(s_sorted + kPartTile);       // regions
+    unsigned int* s_start = s_fill + t.regions;                                         // regions
+    unsigned int* s_gbase = s_start + t.regions;                                        // regions
+    unsigned short* s_reg = reinterpret_cast<unsigned short*>(s_gbase + t.regions);     // kPartTile regions
     __shared__ unsigned int scratch[33];
     const int R = (int)t.regions;
     unsigned int st = 0;
@@ -132,22 +132,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double2* __restrict__ 
             const long long idx = t0 + k * kBlock + threadIdx.x;
             if (idx < n) p[k] = __ldcs(xy + idx);
         }
+        unsigned long long key[kPartPer];
+        unsigned int meta[kPartPer];
 #pragma unroll
         for (int k = 0; k < kPartPer; ++k) {
-            const int j = k * kBlock + threadIdx.x;
-            const long long idx = t0 + j;
-            unsigned int meta = 0xFFFFFFFFu;
+            const long long idx = t0 + k * kBlock + threadIdx.x;
+            meta[k] = 0xFFFFFFFFu;
+            key[k] = 0ull;
             if (idx < n) {
-                const unsigned long long key = project_point<WIDE>(p[k].x, p[k].y, pp);
-                if (key == kInvalidKey) {
+                key[k] = project_point<WIDE>(p[k].x, p[k].y, pp);
+                if (key[k] == kInvalidKey) {
                     st |= kStRange;
                 } else {
-                    const unsigned int r = region_of(key, t);
-                    meta = (r << 12) | atomicAdd(&s_fill[r], 1u);
-                    s_keys[j] = key;
+                    const unsigned int r = region_of(key[k], t);
+                    meta[k] = (r << 12) | atomicAdd(&s_fill[r], 1u);
                 }
             }
-            s_meta[j] = meta;
         }
         __syncthreads();
         const unsigned int total = block_excl_scan_bins(s_fill, R, s_start, scratch);
@@ -155,9 +155,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double2* __restrict__ 
             if (s_fill[r]) s_gbase[r] = atomicAdd(&cursor[r], s_fill[r]);
 #pragma unroll
         for (int k = 0; k < kPartPer; ++k) {
-            const int j = k * kBlock + threadIdx.x;
-            const unsigned int meta = s_meta[j];
-            if (meta != 0xFFFFFFFFu) s_sorted[s_start[meta >> 12] + (meta & 0xFFFu)] = s_keys[j];
+            if (meta[k] != 0xFFFFFFFFu) {
+                const unsigned int r = meta[k] >> 12;
+                const unsigned int pos = s_start[r] + (meta[k] & 0xFFFu);
+                s_sorted[pos] = key[k];
+                s_reg[pos] = (unsigned short)r;
+            }
         }
         __syncthreads();
         for (unsigned int j0 = 0; j0 < total; j0 += kBlock) {  // block-uniform loop (warp ballots inside)
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double2* __restrict__ 
             bool spill = false;
             if (j < total) {
                 key = s_sorted[j];
-                const unsigned int r = region_of(key, t);
+                const unsigned int r = s_reg[j];
                 const unsigned long long pos = (unsigned long long)s_gbase[r] + (j - s_start[r]);
                 if (pos < seg_cap)
                     stage[(unsigned long long)r * seg_cap + pos] = key;
@@ -213,8 +216,211 @@ __device__ __forceinline__ int find_region(const long long* __restrict__ start, 
     return lo;
 }
 
-// Pass 2 of contraction: insert the staged keys, region after region, so the
-// table lines being updated stay in L2.  Equal keys within a warp are merged.
+// Pass 1b of contraction: counting-sort each region's staged keys by bucket
+// (the 2^kBucketBits-slot unit of pass 2) into per-bucket segments of a second
+// staging buffer.  Work items are kInsertItem keys of one region; keys beyond
+// a bucket segment's capacity go to the overflow list.
+__global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsigned long long* __restrict__ stage,
+                                                  unsigned long long seg_cap, const unsigned int* __restrict__ cursor,
+                                                  const long long* __restrict__ item_start, int regions,
+                                                  unsigned long long* __restrict__ stage2, unsigned long long seg2,
+                                                  unsigned int* __restrict__ bcursor, unsigned long long* ovf_key,
+                                                  unsigned int* ovf_cnt, unsigned long long* ovf_n,
+                                                  unsigned long long* work) {
+    __shared__ unsigned long long s_sorted[kInsertItem];
+    __shared__ unsigned short s_b[kInsertItem];
+    __shared__ unsigned int s_fill[kBlock], s_start[kBlock], s_gbase[kBlock];
+    __shared__ unsigned int scratch[33];
+    __shared__ long long s_it;
+    const int bb = (int)t.region_bits - kBucketBits;  // buckets per region: 2^bb <= kBlock
+    const int NB = 1 << bb;
+    const unsigned int local_mask = (1u << t.region_bits) - 1u;
+    const long long total = item_start[regions];
+    for (;;) {
+        if (threadIdx.x == 0) s_it = (long long)atomicAdd(work, 1ull);
+        if (threadIdx.x < NB) s_fill[threadIdx.x] = 0u;
+        __syncthreads();
+        const long long it = s_it;
+        if (it >= total) break;
+        const int r = find_region(item_start, regions, it);
+        const unsigned long long cnt = min((unsigned long long)cursor[r], seg_cap);
+        const unsigned long long k0 = (unsigned long long)(it - item_start[r]) * kInsertItem;
+        const unsigned long long k1 = min(k0 + kInsertItem, cnt);
+        const unsigned long long* seg = stage + (unsigned long long)r * seg_cap;
+        unsigned long long key[kInsertItem / kBlock];
+        unsigned int meta[kInsertItem / kBlock];
+#pragma unroll
+        for (int k = 0; k < (int)(kInsertItem / kBlock); ++k) {
+            const unsigned long long j = k0 + (unsigned long long)(k * kBlock + threadIdx.x);
+            meta[k] = 0xFFFFFFFFu;
+            key[k] = 0ull;
+            if (j < k1) {
+                key[k] = __ldcs(seg + j);
+                const unsigned int b = (tile_hash(key[k]) & local_mask) >> kBucketBits;
+                meta[k] = (b << 12) | atomicAdd(&s_fill[b], 1u);
+            }
+        }
+        __syncthreads();
+        const unsigned int n_items = block_excl_scan_bins(s_fill, NB, s_start, scratch);
+        const unsigned long long g0 = (unsigned long long)r << bb;  // first bucket of region r
+        if (threadIdx.x < NB && s_fill[threadIdx.x])
+            s_gbase[threadIdx.x] = atomicAdd(&bcursor[g0 + threadIdx.x], s_fill[threadIdx.x]);
+#pragma unroll
+        for (int k = 0; k < (int)(kInsertItem / kBlock); ++k) {
+            if (meta[k] != 0xFFFFFFFFu) {
+                const unsigned int b = meta[k] >> 12;
+                const unsigned int pos = s_start[b] + (meta[k] & 0xFFFu);
+                s_sorted[pos] = key[k];
+                s_b[pos] = (unsigned short)b;
+            }
+        }
+        __syncthreads();
+        for (unsigned int j0 = 0; j0 < n_items; j0 += kBlock) {  // block-uniform loop (warp ballots inside)
+            const unsigned int j = j0 + threadIdx.x;
+            unsigned long long k = 0;
+            bool spill = false;
+            if (j < n_items) {
+                k = s_sorted[j];
+                const unsigned int b = s_b[j];
+                const unsigned long long pos = (unsigned long long)s_gbase[b] + (j - s_start[b]);
+                if (pos < seg2)
+                    stage2[(g0 + b) * seg2 + pos] = k;
+                else
+                    spill = true;  // bucket far above its share: to the overflow list
+            }
+            overflow_append(spill, k, 1u, ovf_key, ovf_cnt, ovf_n);
+        }
+        __syncthreads();
+    }
+}
+
+// Add one point to `key` in a bucket held in shared memory (linear probing
+// from the tile's slot within the bucket, as in the global table).  Returns
+// false when the key finds neither itself nor an empty slot within
+// kBucketProbe slots (the bucket is nearly full).
+constexpr unsigned int kBucketProbe = 128;
+__device__ __forceinline__ bool bucket_add(Slot* s_tab, unsigned long long key) {
+    unsigned int i = tile_hash(key) & (kBucketSlots - 1u);
+    for (unsigned int p = 0; p < kBucketProbe; ++p) {
+        unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s_tab[i].key);
+        if (k == kEmptyKey) k = atomicCAS(&s_tab[i].key, kEmptyKey, key);
+        if (k == kEmptyKey || k == key) {
+            atomicAdd(&s_tab[i].count, 1u);
+            return true;
+        }
+        i = (i + 1u) & (kBucketSlots - 1u);
+    }
+    return false;
+}
+
+// Pass 2 of contraction: one bucket at a time per block.  The bucket's slots
+// are copied to shared memory (or cleared, for the first round after a reset,
+// when the table's contents are void), its staged keys are inserted there with
+// shared-memory atomics, and the bucket is written back whole.  New tiles are
+// counted once per bucket, as the growth of its occupied slots.  A key that
+// finds no room within kBucketProbe slots goes to the overflow list and
+// switches the bucket to passing its remaining keys there unprobed; such keys,
+// and a bucket left holding more than `limit` tiles, are counted in *d_full so
+// that the host grows the table.
+constexpr int kInsBlock = 512;
+constexpr int kInsertUnroll = 4;
+__global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ tab, unsigned long long n_buckets,
+                                                            const unsigned long long* __restrict__ stage2,
+                                                            unsigned long long seg2,
+                                                            const unsigned int* __restrict__ bcursor, int fresh,
+                                                            unsigned int limit, unsigned long long* d_newkeys,
+                                                            unsigned long long* d_full, unsigned long long* ovf_key,
+                                                            unsigned int* ovf_cnt, unsigned long long* ovf_n,
+                                                            unsigned long long* work) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Slot* s_tab = reinterpret_cast<Slot*>(smem);  // kBucketSlots slots
+    __shared__ unsigned int s_occ0, s_occ1, s_nfull;
+    __shared__ int s_full;
+    __shared__ unsigned long long s_b;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_b = atomicAdd(work, 1ull);
+            s_occ0 = 0u;
+            s_occ1 = 0u;
+            s_nfull = 0u;
+            s_full = 0;
+        }
+        __syncthreads();
+        const unsigned long long b = s_b;
+        if (b >= n_buckets) break;
+        const unsigned long long n = min((unsigned long long)bcursor[b], seg2);
+        if (n == 0 && !fresh) {  // untouched bucket of a live table: nothing to do
+            __syncthreads();
+            continue;
+        }
+        ulonglong2* g = reinterpret_cast<ulonglong2*>(tab + (b << kBucketBits));
+        ulonglong2* sv = reinterpret_cast<ulonglong2*>(s_tab);
+        if (fresh) {
+            ulonglong2 e;
+            e.x = kEmptyKey;
+            e.y = 0ull;
+            for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) sv[i] = e;
+        } else {
+            // all 4096 16-byte slot copies in flight at once, straight to shared memory
+            for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) {
+                const unsigned int dst = (unsigned int)__cvta_generic_to_shared(sv + i);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g + i) : "memory");
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        unsigned int occ = 0;
+        if (!fresh)
+            for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) occ += sv[i].x != kEmptyKey;
+        occ = __reduce_add_sync(0xFFFFFFFFu, occ);
+        if (lane == 0 && occ) atomicAdd(&s_occ0, occ);
+        const unsigned long long* keys = stage2 + b * seg2;
+        unsigned int full = 0;
+        for (unsigned long long j0 = 0; j0 < n; j0 += (unsigned long long)kInsBlock * kInsertUnroll) {
+            unsigned long long kk[kInsertUnroll];
+#pragma unroll
+            for (int u = 0; u < kInsertUnroll; ++u) {
+                const unsigned long long j = j0 + (unsigned long long)(u * kInsBlock + threadIdx.x);
+                kk[u] = j < n ? __ldcs(keys + j) : kInvalidKey;
+            }
+#pragma unroll
+            for (int u = 0; u < kInsertUnroll; ++u) {
+                bool spill = false;
+                if (kk[u] != kInvalidKey) {
+                    if (*reinterpret_cast<volatile int*>(&s_full) || !bucket_add(s_tab, kk[u])) {
+                        spill = true;
+                        s_full = 1;
+                        ++full;
+                    }
+                }
+                overflow_append(spill, kk[u], 1u, ovf_key, ovf_cnt, ovf_n);
+            }
+        }
+        full = __reduce_add_sync(0xFFFFFFFFu, full);
+        if (lane == 0 && full) atomicAdd(&s_nfull, full);
+        __syncthreads();
+        occ = 0;
+        for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) {
+            const ulonglong2 v = sv[i];
+            occ += v.x != kEmptyKey;
+            g[i] = v;
+        }
+        occ = __reduce_add_sync(0xFFFFFFFFu, occ);
+        if (lane == 0 && occ) atomicAdd(&s_occ1, occ);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_occ1 > s_occ0) atomicAdd(d_newkeys, (unsigned long long)(s_occ1 - s_occ0));
+            const unsigned int over = s_nfull + (s_occ1 > limit ? 1u : 0u);
+            if (over) atomicAdd(d_full, (unsigned long long)over);
+        }
+    }
+}
+
+// Pass 2 of contraction for a round much smaller than the table (a later chunk
+// of a stream): insert the staged keys straight into the table with global
+// atomics, region after region, so the table lines being updated stay in L2,
+// instead of rewriting every bucket.  Equal keys within a warp are merged.
 // New tiles are only created while the table holds fewer than `new_limit`
 // tiles; past it, and for probe sequences longer than the bound, keys go to
 // the overflow list with their counts.  Table plus list always hold the exact
@@ -648,10 +854,11 @@ struct raster_handle {
     long long points = 0;        // points submitted (incl. invalid ones)
 
     // device counters: [0] tiles in the table (D), [1] significant (S),
-    // [2] kept rows, [3] clusters, [4] export rows, [5] overflow entries
+    // [2] kept rows, [3] clusters, [4] export rows, [5] overflow entries,
+    // [6] keys refused by a full bucket
     unsigned long long* d_ctr = nullptr;
     unsigned int* d_status = nullptr;
-    unsigned long long* h_ctr = nullptr;  // pinned mirror: 6 counters, then the status word
+    unsigned long long* h_ctr = nullptr;  // pinned mirror: 7 counters, then the status word
 
     // agglomeration scratch and results (capacity in rows)
     long long agg_cap = 0;
@@ -682,6 +889,14 @@ struct raster_handle {
     unsigned long long* ovf_key = nullptr;
     unsigned int* ovf_cnt = nullptr;
     unsigned long long ovf_cap = 0;    // entries (one per point of a round)
+    // per-bucket key segments of pass 1b and their cursors
+    unsigned long long* stage2 = nullptr;
+    unsigned long long stage2_cap = 0;  // keys
+    unsigned int* bcursor = nullptr;
+    unsigned long long bcursor_cap = 0; // buckets
+    // the table's contents are void (after a reset): the next contraction
+    // round starts its buckets empty instead of reading them
+    bool fresh = false;
 
     unsigned long long* d_work = nullptr;  // work counters of the ordered kernels (8)
 
@@ -727,7 +942,7 @@ void merge_status(raster_handle* h, int s) {
 }
 
 unsigned int max_probe_for(unsigned long long cap) {
-    return (unsigned int)std::min<unsigned long long>(cap, 1ull << 22);
+    return (unsigned int)std::min<unsigned long long>(cap, kBucketSlots);  // probing wraps within a bucket
 }
 
 RegionTable table_of(const raster_handle* h) {
@@ -766,16 +981,19 @@ int fill_table(raster_handle* h, Slot* tab, unsigned long long cap, cudaStream_t
 
 // Read the device counters and status into h_ctr (synchronises the stream).
 int read_counters(raster_handle* h) {
-    RCHECK(h, cudaMemcpyAsync(h->h_ctr, h->d_ctr, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
-    h->h_ctr[6] = 0;
-    RCHECK(h, cudaMemcpyAsync(h->h_ctr + 6, h->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+    RCHECK(h, cudaMemcpyAsync(h->h_ctr, h->d_ctr, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    h->h_ctr[7] = 0;
+    RCHECK(h, cudaMemcpyAsync(h->h_ctr + 7, h->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
     RCHECK(h, cudaStreamSynchronize(h->stream));
-    merge_status(h, status_from_bits((unsigned int)h->h_ctr[6]));
+    merge_status(h, status_from_bits((unsigned int)h->h_ctr[7]));
     return RASTER_OK;
 }
 
 // Replace the table by one of `regions` x 2^bits slots, re-inserting every tile.
 int grow_table(raster_handle* h, unsigned int regions, unsigned int bits) {
+    // capacity is at most 2^32 slots, so at most 4096 regions: k_part keeps
+    // region indices in 16 bits
+    if (regions > 0xFFFFu) return RASTER_E_OOM;
     const unsigned long long new_cap = (unsigned long long)regions << bits;
     Slot* nt = nullptr;
     RCHECK(h, cudaMalloc(&nt, new_cap * sizeof(Slot)));
@@ -790,7 +1008,7 @@ int grow_table(raster_handle* h, unsigned int regions, unsigned int bits) {
     t.regions = regions;
     t.region_bits = bits;
     t.max_probe = max_probe_for(new_cap);
-    if (h->tab && h->cap) {
+    if (h->tab && h->cap && !h->fresh) {
         static int grid = grid_for((const void*)k_rehash, kBlock);
         k_rehash<<<grid, kBlock, 0, h->stream>>>(h->tab, h->cap, t, h->d_status);
         note_launch();
@@ -806,11 +1024,21 @@ int grow_table(raster_handle* h, unsigned int regions, unsigned int bits) {
     h->cap = new_cap;
     h->regions = regions;
     h->region_bits = bits;
+    h->fresh = false;  // the new table is filled
+    return RASTER_OK;
+}
+
+// Make a void table (after a reset) readable: fill it with empty slots.
+int ensure_clean(raster_handle* h) {
+    if (!h->fresh) return RASTER_OK;
+    int rc = fill_table(h, h->tab, h->cap, h->stream);
+    if (rc) return rc;
+    h->fresh = false;
     return RASTER_OK;
 }
 
 size_t part_smem(unsigned int regions) {
-    return (size_t)kPartTile * (8 + 8 + 4) + (size_t)regions * 12;
+    return (size_t)kPartTile * (8 + 2) + (size_t)regions * 12;
 }
 
 int ensure_staging(raster_handle* h, long long n) {
@@ -836,6 +1064,27 @@ int ensure_staging(raster_handle* h, long long n) {
         RCHECK(h, cudaMalloc(&h->ovf_cnt, sizeof(unsigned int) * (size_t)n));
         h->ovf_cap = (unsigned long long)n;
     }
+    // pass 1b: per-bucket segments, 1.25x a bucket's share of a region segment
+    const unsigned long long nb_region = 1ull << (h->region_bits - kBucketBits);
+    const unsigned long long n_buckets = h->cap >> kBucketBits;
+    const unsigned long long seg2 = ((seg + seg / 4) / nb_region + 64 + 1) & ~1ull;
+    if (seg2 * n_buckets > h->stage2_cap) {
+        RCHECK(h, cudaStreamSynchronize(h->stream));
+        if (h->stage2) cudaFree(h->stage2);
+        h->stage2 = nullptr;
+        h->stage2_cap = 0;
+        const unsigned long long cap = seg2 * n_buckets + (seg2 * n_buckets) / 8;
+        RCHECK(h, cudaMalloc(&h->stage2, cap * sizeof(unsigned long long)));
+        h->stage2_cap = cap;
+    }
+    if (n_buckets > h->bcursor_cap) {
+        RCHECK(h, cudaStreamSynchronize(h->stream));
+        if (h->bcursor) cudaFree(h->bcursor);
+        h->bcursor = nullptr;
+        h->bcursor_cap = 0;
+        RCHECK(h, cudaMalloc(&h->bcursor, sizeof(unsigned int) * n_buckets));
+        h->bcursor_cap = n_buckets;
+    }
     if (h->regions > h->cursor_cap) {
         RCHECK(h, cudaStreamSynchronize(h->stream));
         if (h->cursor) cudaFree(h->cursor);
@@ -852,12 +1101,13 @@ int ensure_staging(raster_handle* h, long long n) {
 
 constexpr long long kRoundPoints = 1ll << 30;    // points per contraction round
 constexpr double kNewLimit = 0.8;                // no new tiles beyond this load within a round
-constexpr unsigned int kInsertProbe = 1024;      // longer probe sequences go to the overflow list
+constexpr unsigned int kInsertProbe = 1024;      // global insert: longer probe sequences go to the overflow list
+constexpr double kBucketRound = 0.25;            // rounds of fewer points per table slot insert globally
 
-// One contraction round of n points: pass 1, item prefix, pass 2 (all
-// asynchronous), then one synchronisation to read the table's tile count and
-// the overflow count.  If keys overflowed or the table is too full, grow it
-// and re-insert the overflow list.
+// One contraction round of n points: pass 1, item prefix, pass 1b, pass 2
+// (all asynchronous), then one synchronisation to read the table's tile count
+// and the overflow counts.  If keys overflowed or the table is too full, grow
+// it and re-insert the overflow list.
 template <bool WIDE>
 int contract_round(raster_handle* h, const double* xy, long long n) {
     int rc = ensure_staging(h, n);
@@ -881,20 +1131,53 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
     k_part<WIDE><<<g1, kBlock, smem, h->stream>>>(reinterpret_cast<const double2*>(xy), n, h->pp, t, h->stage_keys,
                                                  seg, h->cursor, h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_status);
     k_region_items<<<1, kBlock, 0, h->stream>>>(h->cursor, (int)h->regions, seg, h->item_start);
-    static int g2 = grid_for((const void*)k_insert, kBlock);
-    RegionTable ti = t;
-    ti.max_probe = std::min<unsigned int>(t.max_probe, kInsertProbe);
-    RCHECK(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), h->stream));
-    k_insert<<<g2, kBlock, 0, h->stream>>>(ti, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
-                                          (unsigned long long)((double)h->cap * kNewLimit), h->d_ctr, h->ovf_key,
-                                          h->ovf_cnt, h->d_ctr + 5, h->d_work);
-    note_launch(3);
-    RCHECK(h, cudaGetLastError());
+    // pass 2: whole buckets in shared memory, unless the round is much smaller
+    // than the table (and the table is live), where rewriting every bucket
+    // would cost more than inserting with global atomics
+    const bool by_bucket = h->fresh || (double)n >= kBucketRound * (double)h->cap;
+    RCHECK(h, cudaMemsetAsync(h->d_ctr + 6, 0, sizeof(unsigned long long), h->stream));
+    if (!by_bucket) {
+        static int g2 = grid_for((const void*)k_insert, kBlock);
+        RegionTable ti = t;
+        ti.max_probe = std::min<unsigned int>(t.max_probe, kInsertProbe);
+        RCHECK(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), h->stream));
+        k_insert<<<g2, kBlock, 0, h->stream>>>(ti, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
+                                              (unsigned long long)((double)h->cap * kNewLimit), h->d_ctr,
+                                              h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work);
+        note_launch(3);
+        RCHECK(h, cudaGetLastError());
+    } else {
+        // pass 1b: by bucket within each region
+        const unsigned long long n_buckets = h->cap >> kBucketBits;
+        const unsigned long long seg2 = (h->stage2_cap / n_buckets) & ~1ull;
+        RCHECK(h, cudaMemsetAsync(h->bcursor, 0, sizeof(unsigned int) * n_buckets, h->stream));
+        RCHECK(h, cudaMemsetAsync(h->d_work, 0, 2 * sizeof(unsigned long long), h->stream));
+        static int gb = grid_for((const void*)k_bucket, kBlock);
+        k_bucket<<<gb, kBlock, 0, h->stream>>>(t, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
+                                              h->stage2, seg2, h->bcursor, h->ovf_key, h->ovf_cnt, h->d_ctr + 5,
+                                              h->d_work);
+        // pass 2: bucket by bucket in shared memory
+        const size_t bsmem = sizeof(Slot) * kBucketSlots;
+        static bool battr = false;
+        if (!battr) {
+            RCHECK(h, cudaFuncSetAttribute(k_insert_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+            battr = true;
+        }
+        static int gi = grid_for((const void*)k_insert_bucket, kInsBlock, bsmem);
+        k_insert_bucket<<<(int)std::min<unsigned long long>((unsigned long long)gi, n_buckets), kInsBlock, bsmem,
+                          h->stream>>>(h->tab, n_buckets, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0,
+                                       (unsigned int)(kNewLimit * kBucketSlots), h->d_ctr, h->d_ctr + 6, h->ovf_key,
+                                       h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
+        h->fresh = false;  // every bucket has been written
+        note_launch(4);
+        RCHECK(h, cudaGetLastError());
+    }
     rc = read_counters(h);
     if (rc) return rc;
-    const unsigned long long D = h->h_ctr[0], ovf = h->h_ctr[5];
+    const unsigned long long D = h->h_ctr[0], ovf = h->h_ctr[5], full = h->h_ctr[6];
     bool grew = false;
-    if ((double)(D + ovf) > kMaxLoad * (double)h->cap) {  // D + ovf bounds the tile count
+    // D + ovf bounds the tile count; a bucket that refused new tiles needs room too
+    if ((double)(D + ovf) > kMaxLoad * (double)h->cap || full > 0) {
         const double need = std::max((double)(D + ovf) / kGrowLoad, 1.5 * (double)h->cap);
         unsigned int regions, bits;
         geometry_for(need, &regions, &bits);
@@ -1135,6 +1418,8 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     const long long D = (long long)h->h_ctr[0];
     h->d_bound = D;
     if (D >= 0x7FFFFFFFll) return RASTER_E_OOM;
+    rc = ensure_clean(h);
+    if (rc) return rc;
     rc = ensure_agg_capacity(h, std::max<long long>(D, 1));
     if (rc) return rc;
     cudaStream_t s = h->stream;
@@ -1309,6 +1594,8 @@ int raster_export_tiles(raster_handle* h, int64_t* key, uint32_t* count, int64_t
     const long long D = (long long)h->h_ctr[0];
     *n_out = D;
     if (capacity < D || (D > 0 && (!key || !count))) return RASTER_E_ARG;
+    rc = ensure_clean(h);
+    if (rc) return rc;
     RCHECK(h, cudaMemsetAsync(h->d_ctr + 4, 0, sizeof(unsigned long long), h->stream));
     static int g_sel = grid_for((const void*)k_select, kBlock);
     k_select<<<g_sel, kBlock, 0, h->stream>>>(h->tab, h->cap, 1u, reinterpret_cast<unsigned long long*>(key), count,
@@ -1325,8 +1612,9 @@ int raster_reset(raster_handle* h, void* stream) {
         // a failed CUDA call may have left the context unusable; try anyway
         cudaGetLastError();
     }
-    int rc = fill_table(h, h->tab, h->cap, h->stream);
-    if (rc) return rc;
+    // the table's contents become void; the next contraction round writes
+    // every bucket, and any other reader fills the table first
+    h->fresh = true;
     RCHECK(h, cudaMemsetAsync(h->d_ctr, 0, 8 * sizeof(unsigned long long), h->stream));
     RCHECK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned int), h->stream));
     h->d_bound = 0;
@@ -1355,7 +1643,8 @@ int raster_destroy(raster_handle* h) {
     void* bufs[] = {h->tab,    h->d_ctr,   h->d_status, h->sig_key, h->sig_cnt, h->sig_slot, h->parent,
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
                     h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
-                    h->ovf_cnt, h->d_work, h->out_slot, h->point_row, h->row_count, h->scan_sums};
+                    h->ovf_cnt, h->d_work, h->out_slot, h->point_row, h->row_count, h->scan_sums,
+                    h->stage2,  h->bcursor};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
