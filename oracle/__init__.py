@@ -30,6 +30,7 @@ _lib = None
 OK = 0
 E_RANGE = 2
 NOISE = np.iinfo(np.int64).min
+CHEBYSHEV, MANHATTAN = 0, 1  # neighbourhood metrics of Sect. 3.2
 
 
 def build(force: bool = False) -> str:
@@ -70,6 +71,8 @@ def _declare(L):
     vp, i64, u32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
     L.oracle_create.restype = vp
     L.oracle_create.argtypes = [dbl, u32, u32]
+    L.oracle_create_ex.restype = vp
+    L.oracle_create_ex.argtypes = [dbl, u32, u32, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.oracle_free.argtypes = [vp]
     L.oracle_add.restype = ctypes.c_int
     L.oracle_add.argtypes = [vp, vp, i64]
@@ -120,10 +123,14 @@ class Result:
 class Oracle:
     """Chunked oracle session: add() per chunk, then finish()."""
 
-    def __init__(self, precision: float, tau: int, mu: int, scale: float | None = None, lib=None):
+    def __init__(self, precision: float, tau: int, mu: int, scale: float | None = None, lib=None,
+                 metric: int = 0, delta: int = 1, groups: bool = False):
         self.L = lib if lib is not None else _load()
         self.scale = scale_of(precision) if scale is None else scale
-        self.h = self.L.oracle_create(self.scale, tau, mu)
+        if metric == CHEBYSHEV and delta == 1 and not groups:
+            self.h = self.L.oracle_create(self.scale, tau, mu)
+        else:
+            self.h = self.L.oracle_create_ex(self.scale, tau, mu, metric, delta, 1 if groups else 0)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -171,9 +178,11 @@ class Oracle:
 
 
 def raster(xy, precision: float, tau: int, mu: int, scale: float | None = None, chunks: int = 1,
-           with_labels: bool = False, lib=None):
-    """Run the oracle on one point set; optionally in ``chunks`` contiguous chunks."""
-    o = Oracle(precision, tau, mu, scale, lib=lib)
+           with_labels: bool = False, lib=None, metric: int = 0, delta: int = 1, groups: bool = False):
+    """Run the oracle on one point set; optionally in ``chunks`` contiguous chunks.
+    ``metric``/``delta`` choose neighbors(u, delta) (Sect. 3.2; default Chebyshev 1)
+    and ``groups`` adds the 2 x 2 group rule of Sect. 3.6."""
+    o = Oracle(precision, tau, mu, scale, lib=lib, metric=metric, delta=delta, groups=groups)
     a = _xy(xy)
     n = a.shape[0]
     for c in range(chunks):
@@ -243,13 +252,15 @@ def project_exact(x: float, scale: float):
     return f
 
 
-def brute_force(keys, counts, tau: int, mu: int):
-    """RASTER agglomeration by all-pairs adjacency: tiles with count >= tau are
-    joined when max(|dx|, |dy|) == 1, via union-find; components with at least
-    mu tiles are kept; the id is the (ix, iy)-smallest member.  O(T^2); tiny T."""
+def brute_force(keys, counts, tau: int, mu: int, metric: int = CHEBYSHEV, delta: int = 1, significant=None):
+    """RASTER agglomeration by all-pairs adjacency: tiles with count >= tau (or
+    those of the boolean mask ``significant``) are joined when their Chebyshev
+    (max(|dx|, |dy|)) or Manhattan (|dx| + |dy|) distance is at most ``delta``,
+    via union-find; components with at least mu tiles are kept; the id is the
+    (ix, iy)-smallest member.  O(T^2); tiny T."""
     keys = np.asarray(keys, dtype=np.int64)
     counts = np.asarray(counts)
-    sig = keys[counts >= tau]
+    sig = keys[np.asarray(significant, dtype=bool)] if significant is not None else keys[counts >= tau]
     ix, iy = unpack(sig)
     t = len(sig)
     parent = list(range(t))
@@ -260,9 +271,13 @@ def brute_force(keys, counts, tau: int, mu: int):
             a = parent[a]
         return a
 
+    def near(a, b):
+        dx, dy = abs(int(ix[a]) - int(ix[b])), abs(int(iy[a]) - int(iy[b]))
+        return (max(dx, dy) if metric == CHEBYSHEV else dx + dy) <= delta
+
     for a in range(t):
         for b in range(a + 1, t):
-            if max(abs(int(ix[a]) - int(ix[b])), abs(int(iy[a]) - int(iy[b]))) == 1:
+            if near(a, b):
                 ra, rb = find(a), find(b)
                 if ra != rb:
                     parent[rb] = ra

@@ -11,9 +11,14 @@
  *                    tile (Alg. 1, first loop; Sect. 3.2), then drop tiles
  *                    with fewer than tau points (Alg. 1, second loop);
  *   agglomeration -- repeatedly pop a significant tile and collect every
- *                    significant tile reachable through neighbours at
- *                    Chebyshev distance 1 (Alg. 1, while loop; Sect. 3.2,
- *                    "eight neighbors"), keeping clusters of at least mu tiles.
+ *                    significant tile reachable through neighbors(u, delta)
+ *                    (Alg. 1, while loop): the tiles at Chebyshev or Manhattan
+ *                    distance at most delta (Sect. 3.2; the paper's own
+ *                    choice, and the default, is Chebyshev distance 1, the
+ *                    eight neighbours), keeping clusters of at least mu tiles.
+ * Optionally (Sect. 3.6, "disadvantageous grid layouts", Fig. 4) the
+ * significant tiles also include every occupied tile of any group of 2 x 2
+ * tiles that holds at least tau points together.
  * Points may arrive in any number of chunks ("Working with huge data sets",
  * Sect. 3.6); the counts only depend on the multiset of points.
  *
@@ -35,6 +40,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <unordered_map>
@@ -82,9 +88,15 @@ bool project(double x, double y, double scale, int64_t *key) {
 
 }  // namespace
 
+const int ORACLE_CHEBYSHEV = 0;
+const int ORACLE_MANHATTAN = 1;
+
 struct oracle_state {
     double scale;
     uint32_t tau, mu;
+    int metric;    /* ORACLE_CHEBYSHEV or ORACLE_MANHATTAN */
+    int delta;     /* neighbourhood radius in tiles */
+    int groups;    /* 1: 2 x 2 groups of Sect. 3.6 also make tiles significant */
     int status;
     int64_t points;
     /* acc of Alg. 1: tile -> number of points */
@@ -101,17 +113,24 @@ struct oracle_state {
 
 extern "C" {
 
-oracle_state *oracle_create(double scale, uint32_t tau, uint32_t mu) {
+oracle_state *oracle_create_ex(double scale, uint32_t tau, uint32_t mu, int metric, int delta, int groups) {
     oracle_state *s = new oracle_state();
     s->scale = scale;
     s->tau = tau;
     s->mu = mu;
+    s->metric = metric;
+    s->delta = delta;
+    s->groups = groups;
     s->status = ORACLE_OK;
     s->points = 0;
     s->finished = false;
     s->n_significant = 0;
     s->n_clusters = 0;
     return s;
+}
+
+oracle_state *oracle_create(double scale, uint32_t tau, uint32_t mu) {
+    return oracle_create_ex(scale, tau, mu, ORACLE_CHEBYSHEV, 1, 0);
 }
 
 void oracle_free(oracle_state *s) { delete s; }
@@ -141,6 +160,28 @@ int oracle_finish(oracle_state *s) {
     std::unordered_set<int64_t> sigma;
     for (const auto &kv : s->acc)
         if (kv.second >= s->tau) sigma.insert(kv.first);
+    /* Sect. 3.6: an occupied tile is also kept when one of the four 2 x 2
+     * groups it belongs to holds at least tau points in total */
+    if (s->groups) {
+        for (const auto &kv : s->acc) {
+            const int64_t x = tile_x(kv.first), y = tile_y(kv.first);
+            bool keep = false;
+            for (int ax = -1; ax <= 0 && !keep; ++ax)
+                for (int ay = -1; ay <= 0 && !keep; ++ay) {
+                    uint64_t total = 0;
+                    for (int gx = 0; gx <= 1; ++gx)
+                        for (int gy = 0; gy <= 1; ++gy) {
+                            const int64_t tx = x + ax + gx, ty = y + ay + gy;
+                            if (tx < -2147483647LL || tx > 2147483646LL) continue;
+                            if (ty < -2147483647LL || ty > 2147483646LL) continue;
+                            auto it = s->acc.find(pack((int32_t)tx, (int32_t)ty));
+                            if (it != s->acc.end()) total += it->second;
+                        }
+                    if (total >= s->tau) keep = true;
+                }
+            if (keep) sigma.insert(kv.first);
+        }
+    }
     s->n_significant = (int64_t)sigma.size();
 
     s->kept_key.clear();
@@ -161,10 +202,11 @@ int oracle_finish(oracle_state *s) {
             int64_t u = visit.front();
             visit.pop_front();
             int32_t ux = tile_x(u), uy = tile_y(u);
-            std::vector<int64_t> ns;
-            for (int dx = -1; dx <= 1; ++dx)
-                for (int dy = -1; dy <= 1; ++dy) {
+            std::vector<int64_t> ns;  /* neighbors(u, delta) in sigma */
+            for (int dx = -s->delta; dx <= s->delta; ++dx)
+                for (int dy = -s->delta; dy <= s->delta; ++dy) {
                     if (dx == 0 && dy == 0) continue;
+                    if (s->metric == ORACLE_MANHATTAN && std::abs(dx) + std::abs(dy) > s->delta) continue;
                     int64_t nx = (int64_t)ux + dx, ny = (int64_t)uy + dy;
                     /* tiles outside the valid index range never exist */
                     if (nx < -2147483647LL || nx > 2147483646LL) continue;

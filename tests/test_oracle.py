@@ -410,3 +410,113 @@ def test_arbitrary_slicing_invariant(seed):
     for _ in range(4):
         borders = sorted(rng.sample(range(-22, 23), rng.randint(1, 6)))
         assert _p_raster_agglomerate(sig, mu, borders) == expect
+
+
+# ---------------------------------------------------------------------------
+# Extensions: the 2 x 2 group rule of Sect. 3.6 and neighbors(u, delta) for a
+# Chebyshev or Manhattan distance delta (Sect. 3.2).
+
+def test_grid_layout_fig4_with_groups():
+    rows = _read_fixture("grid_layout.txt")
+    d = {}
+    for k, v in rows:
+        d.setdefault(k, []).append(v)
+    p, tau, mu = float(d["precision"][0][0]), int(d["tau"][0][0]), int(d["mu"][0][0])
+    split = np.array([[float(a), float(b)] for a, b in d["split"]])
+    r, _ = oracle.raster(split, p, tau, mu, groups=True)
+    assert r.n_significant == int(d["split_groups_significant"][0][0])
+    assert r.n_clusters == int(d["split_groups_clusters"][0][0])
+    # without the rule the same points give nothing (Fig. 4)
+    r, _ = oracle.raster(split, p, tau, mu)
+    assert r.n_significant == 0
+
+
+def _window_significant(keys, counts, tau):
+    """Tiles kept by the 2 x 2 group rule, from window sums over a dense grid
+    (numpy slicing; independent of the oracle's hash-map walk)."""
+    ix, iy = oracle.unpack(keys)
+    x0, y0 = int(ix.min()) - 1, int(iy.min()) - 1
+    grid = np.zeros((int(ix.max()) - x0 + 2, int(iy.max()) - y0 + 2), dtype=np.int64)
+    grid[ix - x0, iy - y0] = counts
+    win = grid[:-1, :-1] + grid[1:, :-1] + grid[:-1, 1:] + grid[1:, 1:]  # anchored at (x, y): x..x+1, y..y+1
+    ok = win >= tau
+    gx, gy = ix - x0, iy - y0
+    # a tile belongs to the windows anchored at (x-1|x, y-1|y)
+    return ok[gx - 1, gy - 1] | ok[gx - 1, gy] | ok[gx, gy - 1] | ok[gx, gy] | (counts >= tau)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_groups_match_window_sums_and_brute_force(seed):
+    rng = random.Random(100 + seed)
+    tiles = _random_tiles(rng, rng.randint(10, 120), span=rng.choice([8, 20]))
+    xy = _points_for_tiles(tiles, 100.0, rng, max_count=4)
+    tau, mu = rng.choice([3, 4, 6]), rng.choice([1, 2, 3])
+    r, o = oracle.raster(xy, 2, tau, mu, groups=True)
+    keys, counts = o.tiles()
+    sig = _window_significant(keys, counts.astype(np.int64), tau)
+    assert r.n_significant == int(sig.sum())
+    bk, bc, bcid, bn = oracle.brute_force(keys, counts, tau, mu, significant=sig)
+    assert np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and np.array_equal(r.count, bc)
+    assert r.n_clusters == bn
+    # the rule only adds tiles: every plain significant tile is still significant
+    rp, _ = oracle.raster(xy, 2, tau, 1)
+    assert set(rp.key.tolist()) <= set(_kept_all(xy, tau).tolist())
+
+
+def _kept_all(xy, tau):
+    r, _ = oracle.raster(xy, 2, tau, 1, groups=True)
+    return r.key
+
+
+@pytest.mark.parametrize("metric,delta", [(oracle.CHEBYSHEV, 2), (oracle.CHEBYSHEV, 3), (oracle.MANHATTAN, 1),
+                                          (oracle.MANHATTAN, 2), (oracle.MANHATTAN, 3)])
+@pytest.mark.parametrize("seed", range(4))
+def test_delta_metrics_match_brute_force(metric, delta, seed):
+    rng = random.Random(200 + seed)
+    tiles = _random_tiles(rng, rng.randint(10, 100), span=rng.choice([10, 25]))
+    xy = _points_for_tiles(tiles, 100.0, rng)
+    tau, mu = rng.choice([1, 2, 3]), rng.choice([1, 2, 4])
+    r, o = oracle.raster(xy, 2, tau, mu, metric=metric, delta=delta)
+    keys, counts = o.tiles()
+    bk, bc, bcid, bn = oracle.brute_force(keys, counts, tau, mu, metric=metric, delta=delta)
+    assert np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and np.array_equal(r.count, bc)
+    assert r.n_clusters == bn
+
+
+def test_manhattan_one_matches_scipy_cross_labelling():
+    """Manhattan distance 1 is 4-connectivity: scipy's labelling with the cross
+    structure gives the same components."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = random.Random(7)
+    tiles = _random_tiles(rng, 150, span=20)
+    xy = _points_for_tiles(tiles, 100.0, rng)
+    r, o = oracle.raster(xy, 2, 2, 1, metric=oracle.MANHATTAN, delta=1)
+    keys, counts = o.tiles()
+    sig = keys[counts >= 2]
+    ix, iy = oracle.unpack(sig)
+    x0, y0 = int(ix.min()), int(iy.min())
+    grid = np.zeros((int(ix.max()) - x0 + 1, int(iy.max()) - y0 + 1), dtype=bool)
+    grid[ix - x0, iy - y0] = True
+    lab, n = ndimage.label(grid, structure=ndimage.generate_binary_structure(2, 1))
+    assert r.n_clusters == n
+    comp = lab[ix - x0, iy - y0]
+    by_key = dict(zip(r.key.tolist(), r.cid.tolist()))
+    for c in range(1, n + 1):
+        members = sig[comp == c]
+        assert len({by_key[int(k)] for k in members}) == 1
+
+
+def test_delta_hand_cases():
+    """Two tiles two steps apart join under Chebyshev 2, not under Chebyshev 1;
+    a knight's move (2, 1) joins under Chebyshev 2 but not under Manhattan 2."""
+    def clusters(tiles, metric, delta):
+        xy = np.array([[(a + 0.5) / 100.0, (b + 0.5) / 100.0] for a, b in tiles])
+        r, _ = oracle.raster(xy, 2, 1, 1, metric=metric, delta=delta)
+        return r.n_clusters
+    assert clusters([(0, 0), (2, 0)], oracle.CHEBYSHEV, 1) == 2
+    assert clusters([(0, 0), (2, 0)], oracle.CHEBYSHEV, 2) == 1
+    assert clusters([(0, 0), (1, 1)], oracle.MANHATTAN, 1) == 2
+    assert clusters([(0, 0), (1, 1)], oracle.MANHATTAN, 2) == 1
+    assert clusters([(0, 0), (2, 1)], oracle.CHEBYSHEV, 2) == 1
+    assert clusters([(0, 0), (2, 1)], oracle.MANHATTAN, 2) == 2
+    assert clusters([(0, 0), (2, 1)], oracle.MANHATTAN, 3) == 1

@@ -23,6 +23,10 @@ MUTANTS = {
     "single_precision_scale": ("v * scale", "v * (double)(float)scale"),
     "lost_increment": ("it->second += 1;", "it->second += (it->second > 3) ? 0 : 1;"),
     "range_off_by_one": ("f <= 2147483646.0", "f <= 2147483647.0"),
+    "group_window_2x1": ("for (int gy = 0; gy <= 1; ++gy)", "for (int gy = 0; gy <= 0; ++gy)"),
+    "group_strict_tau": ("if (total >= s->tau) keep = true;", "if (total > s->tau) keep = true;"),
+    "manhattan_strict": ("std::abs(dx) + std::abs(dy) > s->delta", "std::abs(dx) + std::abs(dy) >= s->delta"),
+    "delta_ignored": ("for (int dx = -s->delta; dx <= s->delta; ++dx)", "for (int dx = -1; dx <= 1; ++dx)"),
 }
 
 
@@ -75,7 +79,30 @@ def _pins_pass(lib) -> bool:
         if not (np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and r.n_clusters == bn
                 and np.array_equal(r.count, bc)):
             return False
+        # neighbors(u, delta) for the other metrics and radii (Sect. 3.2)
+        for metric, delta in ((oracle.CHEBYSHEV, 2), (oracle.MANHATTAN, 1), (oracle.MANHATTAN, 2)):
+            r, _ = oracle.raster(xy, 2, tau, mu, lib=lib, metric=metric, delta=delta)
+            bk, bc, bcid, bn = oracle.brute_force(uk, uc, tau, mu, metric=metric, delta=delta)
+            if not (np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and r.n_clusters == bn):
+                return False
+        # the 2 x 2 group rule (Sect. 3.6) against window sums over a dense grid
+        r, _ = oracle.raster(xy, 2, tau, mu, lib=lib, groups=True)
+        sig = _window_significant(uk, uc.astype(np.int64), tau)
+        bk, bc, bcid, bn = oracle.brute_force(uk, uc, tau, mu, significant=sig)
+        if not (np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and r.n_clusters == bn
+                and r.n_significant == int(sig.sum())):
+            return False
     return True
+
+
+def _window_significant(keys, counts, tau):
+    ix, iy = oracle.unpack(keys)
+    x0, y0 = int(ix.min()) - 1, int(iy.min()) - 1
+    grid = np.zeros((int(ix.max()) - x0 + 2, int(iy.max()) - y0 + 2), dtype=np.int64)
+    grid[ix - x0, iy - y0] = counts
+    ok = (grid[:-1, :-1] + grid[1:, :-1] + grid[:-1, 1:] + grid[1:, 1:]) >= tau
+    gx, gy = ix - x0, iy - y0
+    return ok[gx - 1, gy - 1] | ok[gx - 1, gy] | ok[gx, gy - 1] | ok[gx, gy] | (counts >= tau)
 
 
 def test_real_oracle_passes_compact_pins():
