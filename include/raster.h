@@ -79,6 +79,37 @@ typedef struct {
  * On success *out receives the handle (allocated on the current device). */
 int raster_create(double precision, uint32_t tau, uint32_t mu, raster_handle **out);
 
+/* Neighbourhood metrics for neighbors(u, delta) (Alg. 1; Sect. 3.2: significant
+ * tiles at most a Manhattan or Chebyshev distance of delta steps apart). */
+#define RASTER_CHEBYSHEV 0
+#define RASTER_MANHATTAN 1
+#define RASTER_MAX_DELTA 4
+
+/* Parameters of raster_create_ex.
+ *   precision, tau, mu  as for raster_create.
+ *   metric   RASTER_CHEBYSHEV or RASTER_MANHATTAN (Sect. 3.2).
+ *   delta    1..RASTER_MAX_DELTA: tiles at that distance or less are
+ *            neighbours (Alg. 1 input delta).  raster_create uses Chebyshev 1,
+ *            the eight neighbours.
+ *   groups   0 or 1.  1 adds the post-processing step of Sect. 3.6
+ *            ("disadvantageous grid layouts", Fig. 4): every occupied tile of
+ *            a group of 2 x 2 tiles holding at least tau points together is
+ *            significant too (raster_clusters.n_significant counts them). */
+typedef struct {
+    double precision;
+    uint32_t tau, mu;
+    uint32_t metric;
+    uint32_t delta;
+    uint32_t groups;
+} raster_params;
+
+/* Create a handle with the parameters above (Alg. 1 inputs prec, tau, delta,
+ * mu).  RASTER_E_ARG for an unknown metric, delta outside 1..RASTER_MAX_DELTA,
+ * groups other than 0/1, or any argument raster_create refuses.  Every other
+ * call works on such a handle as on one from raster_create; the batched,
+ * served and fixed-capacity entry points use Chebyshev distance 1 only. */
+int raster_create_ex(const raster_params *params, raster_handle **out);
+
 /* Size the tile table for at least n_tiles distinct tiles (like reserving a
  * hash map; the paper's fixed table budget T, Sect. 3.6).  Optional: the
  * table also grows on demand.  Synchronises the handle's stream. */

@@ -17,9 +17,9 @@ from dataclasses import dataclass
 import torch
 
 from . import _native
-from ._native import NOISE, RasterError, check, lib
+from ._native import CHEBYSHEV, MANHATTAN, NOISE, RasterError, check, lib
 
-__all__ = ["Raster", "Result", "RasterError", "NOISE", "lib", "build", "pack", "unpack"]
+__all__ = ["Raster", "Result", "RasterError", "NOISE", "CHEBYSHEV", "MANHATTAN", "lib", "build", "pack", "unpack"]
 
 
 def build(force: bool = False) -> str:
@@ -88,12 +88,20 @@ def _check_points(xy: torch.Tensor, where: str):
 class Raster:
     """One RASTER problem (precision, tau, mu) with a device-resident tile table."""
 
-    def __init__(self, precision: float, tau: int, mu: int):
+    def __init__(self, precision: float, tau: int, mu: int, metric: int = CHEBYSHEV, delta: int = 1,
+                 groups: bool = False):
+        """metric/delta: neighbors(u, delta) (Sect. 3.2; default Chebyshev 1);
+        groups: the 2 x 2 group rule of Sect. 3.6."""
         self._L = lib()
         h = ctypes.c_void_p()
-        check(self._L.raster_create(float(precision), int(tau), int(mu), ctypes.byref(h)), "raster_create")
+        if metric == CHEBYSHEV and delta == 1 and not groups:
+            check(self._L.raster_create(float(precision), int(tau), int(mu), ctypes.byref(h)), "raster_create")
+        else:
+            p = _native.Params(float(precision), int(tau), int(mu), int(metric), int(delta), 1 if groups else 0)
+            check(self._L.raster_create_ex(ctypes.byref(p), ctypes.byref(h)), "raster_create_ex")
         self._h = h
         self.precision, self.tau, self.mu = precision, tau, mu
+        self.metric, self.delta, self.groups = metric, delta, groups
         self.device = torch.device("cuda", torch.cuda.current_device())
 
     # -- lifecycle ---------------------------------------------------------

@@ -20,6 +20,7 @@ OK = 0
 E_ARG, E_RANGE, E_OOM, E_TABLE_FULL, E_CUDA, E_INTERNAL, E_STATE, E_LIMIT = 1, 2, 3, 4, 5, 6, 7, 8
 STATIC_MAX_POINTS = 524288
 NOISE = -(2 ** 63)
+CHEBYSHEV, MANHATTAN, MAX_DELTA = 0, 1, 4  # RASTER_CHEBYSHEV, RASTER_MANHATTAN, RASTER_MAX_DELTA
 NAMES = {0: "RASTER_OK", 1: "RASTER_E_ARG", 2: "RASTER_E_RANGE", 3: "RASTER_E_OOM", 4: "RASTER_E_TABLE_FULL",
          5: "RASTER_E_CUDA", 6: "RASTER_E_INTERNAL", 7: "RASTER_E_STATE", 8: "RASTER_E_LIMIT"}
 
@@ -29,6 +30,12 @@ class RasterError(RuntimeError):
         self.status = status
         msg = lib().raster_strerror(status).decode() if _lib is not None else ""
         super().__init__(f"{where}: {NAMES.get(status, status)} ({msg})")
+
+
+class Params(ctypes.Structure):
+    """raster_params"""
+    _fields_ = [("precision", ctypes.c_double), ("tau", ctypes.c_uint32), ("mu", ctypes.c_uint32),
+                ("metric", ctypes.c_uint32), ("delta", ctypes.c_uint32), ("groups", ctypes.c_uint32)]
 
 
 class Instance(ctypes.Structure):
@@ -73,6 +80,7 @@ def _declare(L):
     vp, i64, u32, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_int
     sig = {
         "raster_create": (ci, [dbl, u32, u32, ctypes.POINTER(vp)]),
+        "raster_create_ex": (ci, [ctypes.POINTER(Params), ctypes.POINTER(vp)]),
         "raster_reserve": (ci, [vp, i64]),
         "raster_contract": (ci, [vp, vp, i64, vp]),
         "raster_contract_host": (ci, [vp, vp, i64, vp]),

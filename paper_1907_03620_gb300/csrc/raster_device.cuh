@@ -27,6 +27,9 @@ namespace raster {
 constexpr unsigned long long kEmptyKey = 0x8000000000000000ull;
 constexpr unsigned long long kInvalidKey = 0x8000000000000001ull;  // a point that did not project
 constexpr unsigned int kAuxNone = 0xFFFFFFFFu;
+// Marks a tile made significant by a 2 x 2 group (between the group pass and
+// the selection of significant tiles only).
+constexpr unsigned int kAuxGroup = 0xFFFFFFFEu;
 
 // Status bits accumulated on the device (mapped to RASTER_E_* by the host).
 constexpr unsigned int kStRange = 1u;

@@ -59,7 +59,7 @@ __global__ void k_fill_table(Slot* tab, unsigned long long cap) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     ulonglong2 v;
     v.x = kEmptyKey;
-    v.y = 0ull;
+    v.y = (unsigned long long)kAuxNone << 32;  // count 0, aux none
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += stride)
         reinterpret_cast<ulonglong2*>(tab)[i] = v;
 }
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ 
         if (fresh) {
             ulonglong2 e;
             e.x = kEmptyKey;
-            e.y = 0ull;
+            e.y = (unsigned long long)kAuxNone << 32;  // count 0, aux none
             for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) sv[i] = e;
         } else {
             // all 4096 16-byte slot copies in flight at once, straight to shared memory
@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ 
             for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) occ += sv[i].x != kEmptyKey;
         occ = __reduce_add_sync(0xFFFFFFFFu, occ);
         if (lane == 0 && occ) atomicAdd(&s_occ0, occ);
+        __syncthreads();  // every slot counted before any insertion
         const unsigned long long* keys = stage2 + b * seg2;
         unsigned int full = 0;
         for (unsigned long long j0 = 0; j0 < n; j0 += (unsigned long long)kInsBlock * kInsertUnroll) {
@@ -513,7 +514,7 @@ constexpr int kSelItems = 8;
 __global__ void __launch_bounds__(kBlock) k_select(Slot* tab, unsigned long long cap, unsigned int min_count,
                                                   unsigned long long* out_key, unsigned int* out_cnt,
                                                   unsigned int* out_slot, unsigned long long* d_rows,
-                                                  int write_aux) {
+                                                  unsigned long long row_cap, int write_aux, int marked) {
     __shared__ unsigned int scratch[33];
     __shared__ unsigned long long s_base;
     const unsigned long long tile = (unsigned long long)kBlock * kSelItems;
@@ -527,12 +528,14 @@ __global__ void __launch_bounds__(kBlock) k_select(Slot* tab, unsigned long long
             const unsigned long long idx = t0 + (unsigned long long)it * kBlock + threadIdx.x;
             k[it] = kEmptyKey;
             c[it] = 0;
+            bool mark = false;
             if (idx < cap) {
                 const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(tab) + idx);
                 k[it] = v.x;
                 c[it] = (unsigned int)v.y;
+                mark = marked && (unsigned int)(v.y >> 32) == kAuxGroup;
             }
-            if (k[it] != kEmptyKey && c[it] >= min_count) flags |= 1u << it;
+            if (k[it] != kEmptyKey && (c[it] >= min_count || mark)) flags |= 1u << it;
         }
         unsigned int total;
         unsigned int off = block_excl_scan((unsigned int)__popc(flags), scratch, &total);
@@ -544,6 +547,7 @@ __global__ void __launch_bounds__(kBlock) k_select(Slot* tab, unsigned long long
             if (flags & (1u << it)) {
                 const unsigned long long idx = t0 + (unsigned long long)it * kBlock + threadIdx.x;
                 const unsigned long long row = base + off++;
+                if (row >= row_cap) continue;  // more rows than the tile count allows: reported by the host
                 out_key[row] = k[it];
                 out_cnt[row] = c[it];
                 if (out_slot) out_slot[row] = (unsigned int)idx;
@@ -551,6 +555,16 @@ __global__ void __launch_bounds__(kBlock) k_select(Slot* tab, unsigned long long
             }
         }
         __syncthreads();
+    }
+}
+
+// The selection never writes more rows than its buffers hold; if it counted
+// more (the tile count was wrong), clamp the count for the kernels after it
+// and report an internal error.
+__global__ void k_clamp_rows(unsigned long long* d_rows, unsigned long long row_cap, unsigned int* d_status) {
+    if (*d_rows > row_cap) {
+        *d_rows = row_cap;
+        atomicOr(d_status, kStInternal);
     }
 }
 
@@ -576,32 +590,93 @@ __device__ __forceinline__ long long next_chunk(unsigned long long* work, long l
     return c;
 }
 
-// One thread per (significant tile, forward neighbour): (x+1, y-1), (x+1, y),
-// (x+1, y+1), (x, y+1).  Adjacency at Chebyshev distance 1 is symmetric, so
-// these four directions visit every one of the eight neighbour pairs once; the
-// four lookups and unions of a tile run in parallel threads.
+// The forward half of neighbors(u, delta) (Alg. 1): offsets (dx, dy) with
+// dx > 0, or dx = 0 and dy > 0, inside the Chebyshev or Manhattan ball of
+// radius delta (Sect. 3.2).  Adjacency is symmetric, so these visit every
+// neighbour pair once.
+constexpr int kMaxFwd = ((2 * RASTER_MAX_DELTA + 1) * (2 * RASTER_MAX_DELTA + 1) - 1) / 2;
+struct NbrSet {
+    int n;
+    signed char dx[kMaxFwd];
+    signed char dy[kMaxFwd];
+};
+
+// One thread per (significant tile, forward neighbour); a tile's lookups and
+// unions run in parallel threads.  The default neighbourhood (Chebyshev
+// distance 1: (x+1, y-1), (x+1, y), (x+1, y+1), (x, y+1)) is specialised.
+// Significance is read from the slot: the selection wrote each significant
+// tile's row into aux, every other slot holds kAuxNone.
+template <bool GENERAL>
 __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
                                                 const unsigned long long* __restrict__ sig_key, RegionTable t,
-                                                unsigned int tau, int* parent, unsigned long long* work,
+                                                NbrSet nbr, int* parent, unsigned long long* work,
                                                 unsigned int* d_status) {
     __shared__ long long s_chunk;
-    const long long S4 = 4 * (long long)*d_nsig;
+    const int F = GENERAL ? nbr.n : 4;
+    const long long SF = (long long)F * (long long)*d_nsig;
     unsigned int st = 0;
-    for (long long w0 = next_chunk(work, &s_chunk); w0 < S4; w0 = next_chunk(work, &s_chunk)) {
+    for (long long w0 = next_chunk(work, &s_chunk); w0 < SF; w0 = next_chunk(work, &s_chunk)) {
         const long long w = w0 + threadIdx.x;
-        if (w >= S4) continue;
-        const long long i = w >> 2;
-        const int q = (int)(w & 3);
+        if (w >= SF) continue;
+        long long i;
+        int dx, dy;
+        if (GENERAL) {
+            i = w / F;
+            const int q = (int)(w - i * F);
+            dx = nbr.dx[q];
+            dy = nbr.dy[q];
+        } else {
+            i = w >> 2;
+            const int q = (int)(w & 3);
+            dx = q < 3 ? 1 : 0;
+            dy = q < 3 ? q - 1 : 1;
+        }
         const unsigned long long key = sig_key[i];
-        const long long nx = (long long)key_x(key) + (q < 3 ? 1 : 0);
-        const long long ny = (long long)key_y(key) + (q < 3 ? q - 1 : 1);
+        const long long nx = (long long)key_x(key) + dx;
+        const long long ny = (long long)key_y(key) + dy;
         if (nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll) continue;
         const unsigned long long nk = pack_key((int)nx, (int)ny);
         const Slot nb = rt_get(t, nk);
-        if (nb.key != nk || nb.count < tau) continue;
+        if (nb.key != nk || nb.aux == kAuxNone) continue;
         if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
     }
     if (st) atomicOr(d_status, st);
+}
+
+// The post-processing of Sect. 3.6 ("disadvantageous grid layouts"): an
+// occupied tile with fewer than tau points is marked (aux = kAuxGroup) when
+// one of the four 2 x 2 tile groups it belongs to holds at least tau points;
+// the selection then takes it as significant.  One thread per slot reads the
+// counts of the tile's eight neighbours.
+__global__ void __launch_bounds__(kBlock) k_groups(Slot* tab, RegionTable t, unsigned int tau) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < t.cap; i += stride) {
+        const Slot sl = load_slot(&tab[i]);
+        if (sl.key == kEmptyKey || sl.count >= tau) continue;
+        const long long x = key_x(sl.key), y = key_y(sl.key);
+        unsigned long long c[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                c[a][b] = 0ull;
+                const long long nx = x + a - 1, ny = y + b - 1;
+                if (a == 1 && b == 1) {
+                    c[a][b] = sl.count;
+                } else if (nx >= -2147483647ll && nx <= 2147483646ll && ny >= -2147483647ll && ny <= 2147483646ll) {
+                    const unsigned long long nk = pack_key((int)nx, (int)ny);
+                    const Slot nb = rt_get(t, nk);
+                    if (nb.key == nk) c[a][b] = nb.count;
+                }
+            }
+        bool keep = false;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+                keep |= c[a][b] + c[a + 1][b] + c[a][b + 1] + c[a + 1][b + 1] >= tau;
+        if (keep) tab[i].aux = kAuxGroup;
+    }
 }
 
 __global__ void __launch_bounds__(kBlock) k_flatten(const unsigned long long* d_nsig, int* parent,
@@ -693,7 +768,7 @@ __global__ void k_labels(const double2* __restrict__ xy, long long n, ProjParams
             st |= kStRange;
         } else {
             const Slot sl = rt_get(t, key);
-            if (sl.key == key && sl.count >= tau) lab = label_decode(key, sl.aux, cid_rows);
+            if (sl.key == key) lab = label_decode(key, sl.aux, cid_rows);  // kAuxNone decodes to noise
         }
         __stcs(labels + i, lab);
     }
@@ -731,7 +806,7 @@ __global__ void k_group_count(const double2* __restrict__ xy, long long n, ProjP
             st |= kStRange;
         } else {
             const Slot sl = rt_get(t, key);
-            if (sl.key == key && sl.count >= tau && sl.aux != kAuxNone) {
+            if (sl.key == key && sl.aux != kAuxNone) {
                 row = (int)sl.aux;
                 atomicAdd(&row_count[row], 1u);
             }
@@ -841,6 +916,10 @@ int grid_for(const void* kernel, int block, size_t smem = 0) {
 struct raster_handle {
     double precision = 0, scale = 0;
     unsigned int tau = 1, mu = 1;
+    // neighbors(u, delta): forward offsets; `general` unless Chebyshev 1
+    NbrSet nbr{};
+    bool general = false;
+    bool groups = false;  // the 2 x 2 group rule of Sect. 3.6
     ProjParams pp{};
     bool wide = false;
     cudaStream_t stream = nullptr;
@@ -1312,7 +1391,23 @@ const char* raster_strerror(int status) {
 }
 
 int raster_create(double precision, uint32_t tau, uint32_t mu, raster_handle** out) {
-    if (!out || tau == 0 || mu == 0 || !std::isfinite(precision)) return RASTER_E_ARG;
+    raster_params p;
+    p.precision = precision;
+    p.tau = tau;
+    p.mu = mu;
+    p.metric = RASTER_CHEBYSHEV;
+    p.delta = 1;
+    p.groups = 0;
+    return raster_create_ex(&p, out);
+}
+
+int raster_create_ex(const raster_params* params, raster_handle** out) {
+    if (!out || !params) return RASTER_E_ARG;
+    const double precision = params->precision;
+    const uint32_t tau = params->tau, mu = params->mu;
+    if (tau == 0 || mu == 0 || !std::isfinite(precision)) return RASTER_E_ARG;
+    if (params->metric != RASTER_CHEBYSHEV && params->metric != RASTER_MANHATTAN) return RASTER_E_ARG;
+    if (params->delta < 1 || params->delta > RASTER_MAX_DELTA || params->groups > 1) return RASTER_E_ARG;
     *out = nullptr;
     raster_handle* h = new (std::nothrow) raster_handle();
     if (!h) return RASTER_E_OOM;
@@ -1320,6 +1415,21 @@ int raster_create(double precision, uint32_t tau, uint32_t mu, raster_handle** o
     h->scale = scale_of_precision(precision);
     h->tau = tau;
     h->mu = mu;
+    h->groups = params->groups != 0;
+    h->general = !(params->metric == RASTER_CHEBYSHEV && params->delta == 1);
+    {
+        const int d = (int)params->delta;
+        int n = 0;
+        for (int dx = 0; dx <= d; ++dx)
+            for (int dy = -d; dy <= d; ++dy) {
+                if (dx == 0 && dy <= 0) continue;  // forward half only
+                if (params->metric == RASTER_MANHATTAN && dx + std::abs(dy) > d) continue;
+                h->nbr.dx[n] = (signed char)dx;
+                h->nbr.dy[n] = (signed char)dy;
+                ++n;
+            }
+        h->nbr.n = n;
+    }
     if (make_proj_params(h->scale, &h->pp, &h->wide) != RASTER_OK) {
         delete h;
         return RASTER_E_ARG;
@@ -1426,19 +1536,31 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     RCHECK(h, cudaMemsetAsync(h->d_ctr + 1, 0, 4 * sizeof(unsigned long long), s));
     unsigned long long* d_nsig = h->d_ctr + 1;
     static int g_sel = grid_for((const void*)k_select, kBlock);
-    k_select<<<g_sel, kBlock, 0, s>>>(h->tab, h->cap, h->tau, h->sig_key, h->sig_cnt, h->sig_slot, d_nsig, 1);
-    note_launch();
+    if (h->groups) {  // Sect. 3.6: mark tiles of 2 x 2 groups holding >= tau points
+        static int g_grp = grid_for((const void*)k_groups, kBlock);
+        k_groups<<<g_grp, kBlock, 0, s>>>(h->tab, table_of(h), h->tau);
+        note_launch();
+    }
+    k_select<<<g_sel, kBlock, 0, s>>>(h->tab, h->cap, h->tau, h->sig_key, h->sig_cnt, h->sig_slot, d_nsig,
+                                      (unsigned long long)h->agg_cap, 1, h->groups ? 1 : 0);
+    k_clamp_rows<<<1, 1, 0, s>>>(d_nsig, (unsigned long long)h->agg_cap, h->d_status);
+    note_launch(2);
     RCHECK(h, cudaGetLastError());
     static int g_init = grid_for((const void*)k_uf_init, kBlock);
-    static int g_hook = grid_for((const void*)k_hook, kBlock);
+    static int g_hook = grid_for((const void*)k_hook<false>, kBlock);
     static int g_flat = grid_for((const void*)k_flatten, kBlock);
     static int g_stat = grid_for((const void*)k_stats, kBlock);
     static int g_emit = grid_for((const void*)k_emit, kBlock);
     const int lim = (int)std::max<long long>(1, (D + kBlock - 1) / kBlock);
     k_uf_init<<<std::min(g_init, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->csize, h->cmin);
     RCHECK(h, cudaMemsetAsync(h->d_work, 0, 8 * sizeof(unsigned long long), s));
-    k_hook<<<std::min<long long>(g_hook, 4ll * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->tau, h->parent,
-                                                                  h->d_work + 1, h->d_status);
+    const long long F = h->general ? h->nbr.n : 4;  // forward neighbours per significant tile
+    if (h->general)
+        k_hook<true><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->nbr,
+                                                                           h->parent, h->d_work + 1, h->d_status);
+    else
+        k_hook<false><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->nbr,
+                                                                            h->parent, h->d_work + 1, h->d_status);
     k_flatten<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->d_work + 2);
     k_stats<<<std::min(g_stat, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->parent, h->csize, h->cmin,
                                                      h->d_work + 3);
@@ -1599,10 +1721,16 @@ int raster_export_tiles(raster_handle* h, int64_t* key, uint32_t* count, int64_t
     RCHECK(h, cudaMemsetAsync(h->d_ctr + 4, 0, sizeof(unsigned long long), h->stream));
     static int g_sel = grid_for((const void*)k_select, kBlock);
     k_select<<<g_sel, kBlock, 0, h->stream>>>(h->tab, h->cap, 1u, reinterpret_cast<unsigned long long*>(key), count,
-                                              nullptr, h->d_ctr + 4, 0);
+                                              nullptr, h->d_ctr + 4, (unsigned long long)capacity, 0, 0);
     note_launch();
     RCHECK(h, cudaGetLastError());
-    return read_counters(h);
+    rc = read_counters(h);
+    if (rc) return rc;
+    if ((long long)h->h_ctr[4] != D) {  // rows beyond the capacity were not written
+        merge_status(h, RASTER_E_INTERNAL);
+        return RASTER_E_INTERNAL;
+    }
+    return RASTER_OK;
 }
 
 int raster_reset(raster_handle* h, void* stream) {
