@@ -43,7 +43,7 @@ POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 # workload, from one ncu capture with one pass per launch
 # (profiles/raster_500m_dram_per_kernel.md).  Valid only for the kernel
 # sources it was measured with; reported as null otherwise.
-MEASURED_CONTRACT_TRAFFIC = {"sources": "a965716eb866991d", "workload": "raster-500m", "bytes": 26_413_000_000}
+MEASURED_CONTRACT_TRAFFIC = {"sources": "0890f6916daa4b79", "workload": "raster-500m", "bytes": 31_519_000_000}
 
 
 def kernel_sources_digest() -> str:
@@ -501,7 +501,7 @@ def run_gpu(args):
     if (not args.points and args.workload == "500m"
             and kernel_sources_digest() == MEASURED_CONTRACT_TRAFFIC["sources"]):
         traffic = MEASURED_CONTRACT_TRAFFIC["bytes"]
-    roofline = {"bound": "hbm", "kernel": "contraction phase: k_part + k_region_items + k_insert",
+    roofline = {"bound": "hbm", "kernel": "contraction phase: k_part + k_region_items + k_bucket + k_insert_bucket",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"] + " (copy bandwidth)",
                 "traffic": traffic, "traffic_unit": "bytes per contraction phase (ncu dram__bytes read+write)",
@@ -574,6 +574,37 @@ def run_gpu(args):
             "algorithmic": "16 B/point read + 8 B/grouped point + 8 B/row written",
             "frac": g_bytes / (gms / 1e3) / 1e9 / peaks["hbm_gbs"]}
         del gbuf, gidx
+
+    # the extensions on the same workload and step: the 2 x 2 group rule
+    # (Sect. 3.6) and other neighbourhoods neighbors(u, delta) (Sect. 3.2)
+    if not args.profile and not args.no_forms:
+        ext = {}
+        for name, kw in (("groups_2x2", dict(groups=True)), ("chebyshev_delta2", dict(delta=2)),
+                         ("manhattan_delta2", dict(metric=R.MANHATTAN, delta=2))):
+            rx = R.Raster(w.precision, w.tau, w.mu, **kw)
+            times = {"contract": [], "agglomerate": [], "labels": []}
+            for rep in range(4):
+                e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+                e0.record(stream)
+                rx.reset()
+                rx.contract(xy)
+                e1.record(stream)
+                resx = rx.agglomerate(copy=False, raw=True)
+                e2.record(stream)
+                rx.point_labels(xy, out=labels)
+                e3.record(stream)
+                torch.cuda.synchronize()
+                if rep:
+                    times["contract"].append(e0.elapsed_time(e1))
+                    times["agglomerate"].append(e1.elapsed_time(e2))
+                    times["labels"].append(e2.elapsed_time(e3))
+            ms = {k: statistics.mean(v) for k, v in times.items()}
+            step_ms = max_over_ranks(sum(ms.values()), dev)
+            ext[name] = {"value": whole_job_rate(world, w.n, step_ms / 1e3), "unit": "points/s", "ms_per_step": step_ms,
+                         "phases_ms": ms, "n_significant": resx.n_significant, "n_clusters": resx.n_clusters,
+                         "kept_tiles": int(resx.key.numel())}
+            rx.close()
+        line["extensions"] = ext
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     if not args.no_e2e and not args.profile:

@@ -647,10 +647,14 @@ __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsi
 // occupied tile with fewer than tau points is marked (aux = kAuxGroup) when
 // one of the four 2 x 2 tile groups it belongs to holds at least tau points;
 // the selection then takes it as significant.  One thread per slot reads the
-// counts of the tile's eight neighbours.
-__global__ void __launch_bounds__(kBlock) k_groups(Slot* tab, RegionTable t, unsigned int tau) {
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < t.cap; i += stride) {
+// counts of the tile's eight neighbours; slots are taken in order, chunk by
+// chunk, so the lookups stay within the few regions in flight.
+__global__ void __launch_bounds__(kBlock) k_groups(Slot* tab, RegionTable t, unsigned int tau,
+                                                  unsigned long long* work) {
+    __shared__ long long s_chunk;
+    for (long long c0 = next_chunk(work, &s_chunk); c0 < (long long)t.cap; c0 = next_chunk(work, &s_chunk)) {
+        const unsigned long long i = (unsigned long long)c0 + threadIdx.x;
+        if (i >= t.cap) continue;
         const Slot sl = load_slot(&tab[i]);
         if (sl.key == kEmptyKey || sl.count >= tau) continue;
         const long long x = key_x(sl.key), y = key_y(sl.key);
@@ -1182,6 +1186,8 @@ constexpr long long kRoundPoints = 1ll << 30;    // points per contraction round
 constexpr double kNewLimit = 0.8;                // no new tiles beyond this load within a round
 constexpr unsigned int kInsertProbe = 1024;      // global insert: longer probe sequences go to the overflow list
 constexpr double kBucketRound = 0.25;            // rounds of fewer points per table slot insert globally
+constexpr double kRefitRatio = 1.5;              // a grown table this much larger than needed is rebuilt
+constexpr double kPreGrow = 4.0;                 // grow before a round whose estimate is this far past kMaxLoad
 
 // One contraction round of n points: pass 1, item prefix, pass 1b, pass 2
 // (all asynchronous), then one synchronisation to read the table's tile count
@@ -1189,7 +1195,24 @@ constexpr double kBucketRound = 0.25;            // rounds of fewer points per t
 // it and re-insert the overflow list.
 template <bool WIDE>
 int contract_round(raster_handle* h, const double* xy, long long n) {
-    int rc = ensure_staging(h, n);
+    // A round far larger than the table (the first call into the initial
+    // table, say) grows it first: a full bucket would pass its remaining keys
+    // to the overflow list one block at a time.  D + n/2 estimates the tiles
+    // after the round; a table that turns out far too large is rebuilt
+    // smaller below.
+    int rc;
+    bool grew = false;
+    const double est = (double)h->d_bound + 0.5 * (double)n;
+    if (est > kPreGrow * kMaxLoad * (double)h->cap) {
+        unsigned int regions, bits;
+        geometry_for(est / kGrowLoad, &regions, &bits);
+        if (((unsigned long long)regions << bits) <= (1ull << 32)) {
+            rc = grow_table(h, regions, bits);
+            if (rc) return rc;
+            grew = true;
+        }
+    }
+    rc = ensure_staging(h, n);
     if (rc) return rc;
     const unsigned long long seg = h->stage_cap / h->regions;
     RegionTable t = table_of(h);
@@ -1254,7 +1277,6 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
     rc = read_counters(h);
     if (rc) return rc;
     const unsigned long long D = h->h_ctr[0], ovf = h->h_ctr[5], full = h->h_ctr[6];
-    bool grew = false;
     // D + ovf bounds the tile count; a bucket that refused new tiles needs room too
     if ((double)(D + ovf) > kMaxLoad * (double)h->cap || full > 0) {
         const double need = std::max((double)(D + ovf) / kGrowLoad, 1.5 * (double)h->cap);
@@ -1265,25 +1287,23 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
         if (rc) return rc;
         grew = true;
     }
-    {
-        if (ovf > 0) {
-            static int g3 = grid_for((const void*)k_reinsert, kBlock);
-            k_reinsert<<<g3, kBlock, 0, h->stream>>>(table_of(h), h->ovf_key, h->ovf_cnt, ovf, h->d_ctr,
-                                                    h->d_status);
-            note_launch();
-            RCHECK(h, cudaGetLastError());
-            rc = read_counters(h);
-            if (rc) return rc;
-            // the growth estimate counted every overflowed point as a new tile;
-            // rebuild a table that ended up far larger than the tiles need
-            const double fit = (double)h->h_ctr[0] / kGrowLoad;
-            if (grew && (double)h->cap > 2.0 * fit && (double)h->cap > (double)(1ull << 20)) {
-                unsigned int regions, bits;
-                geometry_for(fit, &regions, &bits);
-                rc = grow_table(h, regions, bits);
-                if (rc) return rc;
-            }
-        }
+    if (ovf > 0) {
+        static int g3 = grid_for((const void*)k_reinsert, kBlock);
+        k_reinsert<<<g3, kBlock, 0, h->stream>>>(table_of(h), h->ovf_key, h->ovf_cnt, ovf, h->d_ctr, h->d_status);
+        note_launch();
+        RCHECK(h, cudaGetLastError());
+        rc = read_counters(h);
+        if (rc) return rc;
+    }
+    // the growth estimates counted overflowed points, or half the round's
+    // points, as new tiles: rebuild a grown table that ended up far larger
+    // than the tiles need (a table the caller reserved is left alone)
+    const double fit = (double)h->h_ctr[0] / kGrowLoad;
+    if (grew && (double)h->cap > kRefitRatio * fit && (double)h->cap > (double)(1ull << 20)) {
+        unsigned int regions, bits;
+        geometry_for(fit, &regions, &bits);
+        rc = grow_table(h, regions, bits);
+        if (rc) return rc;
     }
     h->d_bound = (long long)h->h_ctr[0];
     return RASTER_OK;
@@ -1538,7 +1558,8 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     static int g_sel = grid_for((const void*)k_select, kBlock);
     if (h->groups) {  // Sect. 3.6: mark tiles of 2 x 2 groups holding >= tau points
         static int g_grp = grid_for((const void*)k_groups, kBlock);
-        k_groups<<<g_grp, kBlock, 0, s>>>(h->tab, table_of(h), h->tau);
+        RCHECK(h, cudaMemsetAsync(h->d_work + 6, 0, sizeof(unsigned long long), s));
+        k_groups<<<g_grp, kBlock, 0, s>>>(h->tab, table_of(h), h->tau, h->d_work + 6);
         note_launch();
     }
     k_select<<<g_sel, kBlock, 0, s>>>(h->tab, h->cap, h->tau, h->sig_key, h->sig_cnt, h->sig_slot, d_nsig,
