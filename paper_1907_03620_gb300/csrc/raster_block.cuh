@@ -17,10 +17,11 @@ __device__ __forceinline__ unsigned int warp_incl_scan(unsigned int v) {
     return v;
 }
 
-// Exclusive block scan of v (blockDim.x == kScanBlock); returns the prefix and
-// writes the block total to *total.  Uses `scratch` (>= 33 words).
+// Exclusive block scan of v (blockDim.x == BLOCK, at most 1024); returns the
+// prefix and writes the block total to *total.  Uses `scratch` (>= 33 words).
+template <int BLOCK = kScanBlock>
 __device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned int* scratch, unsigned int* total) {
-    constexpr int kBlock = kScanBlock;
+    constexpr int kBlock = BLOCK;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned int incl = warp_incl_scan(v);
     if (lane == 31) scratch[warp] = incl;

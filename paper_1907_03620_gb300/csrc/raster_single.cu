@@ -74,15 +74,16 @@ constexpr int kPartTile = 2048;
 constexpr int kPartPer = kPartTile / kBlock;
 constexpr long long kInsertItem = 2048;
 
+template <int BLOCK = kBlock>
 __device__ __forceinline__ unsigned int block_excl_scan_bins(unsigned int* bins, int nbins, unsigned int* start,
                                                              unsigned int* scratch) {
     // each thread owns a contiguous run of bins
-    const int per = (nbins + kBlock - 1) / kBlock;
+    const int per = (nbins + BLOCK - 1) / BLOCK;
     const int b0 = threadIdx.x * per;
     unsigned int sum = 0;
     for (int b = b0; b < min(b0 + per, nbins); ++b) sum += bins[b];
     unsigned int total;
-    unsigned int off = block_excl_scan(sum, scratch, &total);
+    unsigned int off = block_excl_scan<BLOCK>(sum, scratch, &total);
     for (int b = b0; b < min(b0 + per, nbins); ++b) {
         start[b] = off;
         off += bins[b];
