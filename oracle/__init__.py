@@ -72,7 +72,7 @@ def _declare(L):
     L.oracle_create.restype = vp
     L.oracle_create.argtypes = [dbl, u32, u32]
     L.oracle_create_ex.restype = vp
-    L.oracle_create_ex.argtypes = [dbl, u32, u32, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.oracle_create_ex.argtypes = [dbl, u32, u32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.oracle_free.argtypes = [vp]
     L.oracle_add.restype = ctypes.c_int
     L.oracle_add.argtypes = [vp, vp, i64]
@@ -88,8 +88,8 @@ def _declare(L):
     L.oracle_copy_kept.argtypes = [vp, vp, vp, vp]
     L.oracle_labels.restype = ctypes.c_int
     L.oracle_labels.argtypes = [vp, vp, i64, vp]
-    L.oracle_project.argtypes = [vp, i64, dbl, vp, vp]
-    L.oracle_count_keys.argtypes = [vp, i64, dbl, vp, i64, vp]
+    L.oracle_project.argtypes = [vp, i64, dbl, vp, vp, ctypes.c_int]
+    L.oracle_count_keys.argtypes = [vp, i64, dbl, vp, i64, vp, ctypes.c_int]
     L.oracle_point_groups.restype = i64
     L.oracle_point_groups.argtypes = [vp, vp, i64, vp, vp, i64]
 
@@ -104,7 +104,7 @@ def scale_of(precision: float) -> float:
 
 def _xy(xy) -> np.ndarray:
     a = np.ascontiguousarray(xy, dtype=np.float64)
-    assert a.ndim == 2 and a.shape[1] == 2
+    assert a.ndim == 2 and a.shape[1] in (2, 3)
     return a
 
 
@@ -124,13 +124,17 @@ class Oracle:
     """Chunked oracle session: add() per chunk, then finish()."""
 
     def __init__(self, precision: float, tau: int, mu: int, scale: float | None = None, lib=None,
-                 metric: int = 0, delta: int = 1, groups: bool = False):
+                 metric: int = 0, delta: int = 1, groups: bool = False, dims: int = 2):
+        """dims: coordinates per point, 2 or 3 (Sect. 3.6, higher dimensions);
+        the 2 x 2 group rule applies to two coordinates only."""
+        assert dims in (2, 3) and not (groups and dims == 3)
         self.L = lib if lib is not None else _load()
         self.scale = scale_of(precision) if scale is None else scale
-        if metric == CHEBYSHEV and delta == 1 and not groups:
+        self.dims = dims
+        if metric == CHEBYSHEV and delta == 1 and not groups and dims == 2:
             self.h = self.L.oracle_create(self.scale, tau, mu)
         else:
-            self.h = self.L.oracle_create_ex(self.scale, tau, mu, metric, delta, 1 if groups else 0)
+            self.h = self.L.oracle_create_ex(self.scale, tau, mu, metric, delta, 1 if groups else 0, dims)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -139,6 +143,7 @@ class Oracle:
 
     def add(self, xy) -> int:
         a = _xy(xy)
+        assert a.shape[1] == self.dims
         return self.L.oracle_add(self.h, a.ctypes.data, a.shape[0])
 
     def finish(self) -> Result:
@@ -163,6 +168,7 @@ class Oracle:
         """RASTER' (Sect. 3.4): (row_start, point_index) over the kept tiles in
         the order of finish()'s rows, indices increasing within a row."""
         a = _xy(xy)
+        assert a.shape[1] == self.dims
         k = self.L.oracle_n_kept(self.h)
         row_start = np.empty(k + 1, np.int64)
         idx = np.empty(max(a.shape[0], 1), np.int64)
@@ -172,6 +178,7 @@ class Oracle:
 
     def labels(self, xy) -> tuple[int, np.ndarray]:
         a = _xy(xy)
+        assert a.shape[1] == self.dims
         out = np.empty(a.shape[0], np.int64)
         st = self.L.oracle_labels(self.h, a.ctypes.data, a.shape[0], out.ctypes.data)
         return st, out
@@ -182,8 +189,8 @@ def raster(xy, precision: float, tau: int, mu: int, scale: float | None = None, 
     """Run the oracle on one point set; optionally in ``chunks`` contiguous chunks.
     ``metric``/``delta`` choose neighbors(u, delta) (Sect. 3.2; default Chebyshev 1)
     and ``groups`` adds the 2 x 2 group rule of Sect. 3.6."""
-    o = Oracle(precision, tau, mu, scale, lib=lib, metric=metric, delta=delta, groups=groups)
     a = _xy(xy)
+    o = Oracle(precision, tau, mu, scale, lib=lib, metric=metric, delta=delta, groups=groups, dims=a.shape[1])
     n = a.shape[0]
     for c in range(chunks):
         o.add(a[n * c // chunks: n * (c + 1) // chunks])
@@ -198,7 +205,7 @@ def project(xy, scale: float) -> tuple[np.ndarray, np.ndarray]:
     a = _xy(xy)
     keys = np.empty(a.shape[0], np.int64)
     ok = np.empty(a.shape[0], np.uint8)
-    _load().oracle_project(a.ctypes.data, a.shape[0], scale, keys.ctypes.data, ok.ctypes.data)
+    _load().oracle_project(a.ctypes.data, a.shape[0], scale, keys.ctypes.data, ok.ctypes.data, a.shape[1])
     return keys, ok.astype(bool)
 
 
@@ -206,7 +213,8 @@ def count_keys(xy, scale: float, keys) -> np.ndarray:
     a = _xy(xy)
     k = np.ascontiguousarray(keys, dtype=np.int64)
     out = np.empty(k.shape[0], np.uint64)
-    _load().oracle_count_keys(a.ctypes.data, a.shape[0], scale, k.ctypes.data, k.shape[0], out.ctypes.data)
+    _load().oracle_count_keys(a.ctypes.data, a.shape[0], scale, k.ctypes.data, k.shape[0], out.ctypes.data,
+                              a.shape[1])
     return out
 
 
@@ -221,6 +229,19 @@ def pack(ix, iy):
 def unpack(key):
     key = np.asarray(key, dtype=np.int64)
     return (key >> 32).astype(np.int64), (key & 0xFFFFFFFF).astype(np.uint32).astype(np.int32).astype(np.int64)
+
+
+BIAS3 = 1 << 20  # three coordinates: 21-bit fields, each index offset by 2^20
+
+
+def pack3(ix, iy, iz):
+    ix, iy, iz = (np.asarray(v, dtype=np.int64) for v in (ix, iy, iz))
+    return ((ix + BIAS3) << 42) | ((iy + BIAS3) << 21) | (iz + BIAS3)
+
+
+def unpack3(key):
+    key = np.asarray(key, dtype=np.int64)
+    return tuple(((key >> sh) & 0x1FFFFF) - BIAS3 for sh in (42, 21, 0))
 
 
 def tile_order(key) -> np.ndarray:
@@ -252,16 +273,17 @@ def project_exact(x: float, scale: float):
     return f
 
 
-def brute_force(keys, counts, tau: int, mu: int, metric: int = CHEBYSHEV, delta: int = 1, significant=None):
+def brute_force(keys, counts, tau: int, mu: int, metric: int = CHEBYSHEV, delta: int = 1, significant=None,
+                dims: int = 2):
     """RASTER agglomeration by all-pairs adjacency: tiles with count >= tau (or
     those of the boolean mask ``significant``) are joined when their Chebyshev
-    (max(|dx|, |dy|)) or Manhattan (|dx| + |dy|) distance is at most ``delta``,
-    via union-find; components with at least mu tiles are kept; the id is the
-    (ix, iy)-smallest member.  O(T^2); tiny T."""
+    (largest coordinate difference) or Manhattan (sum of differences) distance
+    is at most ``delta``, via union-find; components with at least mu tiles are
+    kept; the id is the lexicographically smallest member.  O(T^2); tiny T."""
     keys = np.asarray(keys, dtype=np.int64)
     counts = np.asarray(counts)
     sig = keys[np.asarray(significant, dtype=bool)] if significant is not None else keys[counts >= tau]
-    ix, iy = unpack(sig)
+    coords = np.stack(unpack3(sig) if dims == 3 else unpack(sig), axis=1).astype(np.int64)
     t = len(sig)
     parent = list(range(t))
 
@@ -272,8 +294,8 @@ def brute_force(keys, counts, tau: int, mu: int, metric: int = CHEBYSHEV, delta:
         return a
 
     def near(a, b):
-        dx, dy = abs(int(ix[a]) - int(ix[b])), abs(int(iy[a]) - int(iy[b]))
-        return (max(dx, dy) if metric == CHEBYSHEV else dx + dy) <= delta
+        d = np.abs(coords[a] - coords[b])
+        return int(d.max() if metric == CHEBYSHEV else d.sum()) <= delta
 
     for a in range(t):
         for b in range(a + 1, t):
@@ -290,10 +312,10 @@ def brute_force(keys, counts, tau: int, mu: int, metric: int = CHEBYSHEV, delta:
         if len(members) < mu:
             continue
         n_clusters += 1
-        best = min(members, key=lambda m: (int(ix[m]), int(iy[m])))
+        best = min(members, key=lambda m: tuple(int(c) for c in coords[m]))
         for m in members:
             rows.append((int(sig[m]), int(sig[best])))
-    rows.sort(key=lambda r: (r[0] >> 32, np.int32(np.uint32(r[0] & 0xFFFFFFFF))))
+    rows.sort(key=lambda r: r[0] if dims == 3 else (r[0] >> 32, np.int32(np.uint32(r[0] & 0xFFFFFFFF))))
     cnt_of = {int(k): int(c) for k, c in zip(keys, counts)}
     key = np.array([r[0] for r in rows], dtype=np.int64)
     cid = np.array([r[1] for r in rows], dtype=np.int64)

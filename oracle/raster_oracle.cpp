@@ -16,6 +16,9 @@
  *                    distance at most delta (Sect. 3.2; the paper's own
  *                    choice, and the default, is Chebyshev distance 1, the
  *                    eight neighbours), keeping clusters of at least mu tiles.
+ * Points have two coordinates, or three (Sect. 3.6, "Generalizing to Higher
+ * Dimensions": the same method on d-dimensional tiles, whose neighbours at
+ * Chebyshev distance 1 are the 3^d - 1 surrounding tiles).
  * Optionally (Sect. 3.6, "disadvantageous grid layouts", Fig. 4) the
  * significant tiles also include every occupied tile of any group of 2 x 2
  * tiles that holds at least tau points together.
@@ -32,6 +35,9 @@
  *     out-of-range coordinate is an error (ORACLE_RANGE) and that point is
  *     skipped;
  *   - key = (int64)ix << 32 | (uint32)iy;
+ *   - three coordinates: each index must lie in [-(2^20 - 1), 2^20 - 2];
+ *     key = (ix + 2^20) << 42 | (iy + 2^20) << 21 | (iz + 2^20), so integer
+ *     order of keys is (ix, iy, iz) order;
  *   - significant: count >= tau; kept: cluster size (in tiles) >= mu;
  *   - cluster id = key of the cluster's smallest tile in (ix, iy)
  *     lexicographic order; noise label = INT64_MIN;
@@ -86,6 +92,52 @@ bool project(double x, double y, double scale, int64_t *key) {
     return true;
 }
 
+/* Three coordinates: 21-bit fields, each index offset by 2^20. */
+const int64_t BIAS3 = (int64_t)1 << 20;
+const int64_t MIN3 = -(BIAS3 - 1), MAX3 = BIAS3 - 2;
+
+int64_t pack3(int64_t ix, int64_t iy, int64_t iz) {
+    return ((ix + BIAS3) << 42) | ((iy + BIAS3) << 21) | (iz + BIAS3);
+}
+int64_t tile3(int64_t key, int axis) { return ((key >> (42 - 21 * axis)) & 0x1FFFFF) - BIAS3; }
+
+bool project_coord3(double v, double scale, int64_t *out) {
+    volatile double product = scale * v; /* one rounded multiply */
+    double f = std::floor(product);
+    if (!(f >= (double)MIN3 && f <= (double)MAX3)) return false;
+    *out = (int64_t)f;
+    return true;
+}
+
+/* Project point i of an array of `dims` coordinates per point. */
+bool project_point(const double *xy, int64_t i, int dims, double scale, int64_t *key) {
+    if (dims == 3) {
+        int64_t c[3];
+        for (int a = 0; a < 3; ++a)
+            if (!project_coord3(xy[3 * i + a], scale, &c[a])) return false;
+        *key = pack3(c[0], c[1], c[2]);
+        return true;
+    }
+    return project(xy[2 * i], xy[2 * i + 1], scale, key);
+}
+
+/* The tile at offset (dx, dy, dz) from u, if its indices are valid. */
+bool neighbour_key(int64_t u, int dx, int dy, int dz, int dims, int64_t *out) {
+    if (dims == 3) {
+        const int64_t n[3] = {tile3(u, 0) + dx, tile3(u, 1) + dy, tile3(u, 2) + dz};
+        for (int a = 0; a < 3; ++a)
+            if (n[a] < MIN3 || n[a] > MAX3) return false;
+        *out = pack3(n[0], n[1], n[2]);
+        return true;
+    }
+    /* tiles outside the valid index range never exist */
+    int64_t nx = (int64_t)tile_x(u) + dx, ny = (int64_t)tile_y(u) + dy;
+    if (nx < -2147483647LL || nx > 2147483646LL) return false;
+    if (ny < -2147483647LL || ny > 2147483646LL) return false;
+    *out = pack((int32_t)nx, (int32_t)ny);
+    return true;
+}
+
 }  // namespace
 
 const int ORACLE_CHEBYSHEV = 0;
@@ -97,6 +149,7 @@ struct oracle_state {
     int metric;    /* ORACLE_CHEBYSHEV or ORACLE_MANHATTAN */
     int delta;     /* neighbourhood radius in tiles */
     int groups;    /* 1: 2 x 2 groups of Sect. 3.6 also make tiles significant */
+    int dims;      /* coordinates per point: 2 or 3 */
     int status;
     int64_t points;
     /* acc of Alg. 1: tile -> number of points */
@@ -111,9 +164,13 @@ struct oracle_state {
     std::unordered_map<int64_t, int64_t> cid_of;  /* kept tile -> cluster id */
 };
 
+/* (ix, iy[, iz]) lexicographic order of two keys. */
+static bool before(const oracle_state *s, int64_t a, int64_t b) { return s->dims == 3 ? a < b : tile_less(a, b); }
+
 extern "C" {
 
-oracle_state *oracle_create_ex(double scale, uint32_t tau, uint32_t mu, int metric, int delta, int groups) {
+oracle_state *oracle_create_ex(double scale, uint32_t tau, uint32_t mu, int metric, int delta, int groups,
+                               int dims) {
     oracle_state *s = new oracle_state();
     s->scale = scale;
     s->tau = tau;
@@ -121,6 +178,7 @@ oracle_state *oracle_create_ex(double scale, uint32_t tau, uint32_t mu, int metr
     s->metric = metric;
     s->delta = delta;
     s->groups = groups;
+    s->dims = dims;
     s->status = ORACLE_OK;
     s->points = 0;
     s->finished = false;
@@ -130,7 +188,7 @@ oracle_state *oracle_create_ex(double scale, uint32_t tau, uint32_t mu, int metr
 }
 
 oracle_state *oracle_create(double scale, uint32_t tau, uint32_t mu) {
-    return oracle_create_ex(scale, tau, mu, ORACLE_CHEBYSHEV, 1, 0);
+    return oracle_create_ex(scale, tau, mu, ORACLE_CHEBYSHEV, 1, 0, 2);
 }
 
 void oracle_free(oracle_state *s) { delete s; }
@@ -139,7 +197,7 @@ void oracle_free(oracle_state *s) { delete s; }
 int oracle_add(oracle_state *s, const double *xy, int64_t n) {
     for (int64_t i = 0; i < n; ++i) {
         int64_t key;
-        if (!project(xy[2 * i], xy[2 * i + 1], s->scale, &key)) {
+        if (!project_point(xy, i, s->dims, s->scale, &key)) {
             s->status = ORACLE_RANGE;
             continue;
         }
@@ -162,7 +220,7 @@ int oracle_finish(oracle_state *s) {
         if (kv.second >= s->tau) sigma.insert(kv.first);
     /* Sect. 3.6: an occupied tile is also kept when one of the four 2 x 2
      * groups it belongs to holds at least tau points in total */
-    if (s->groups) {
+    if (s->groups && s->dims == 2) {
         for (const auto &kv : s->acc) {
             const int64_t x = tile_x(kv.first), y = tile_y(kv.first);
             bool keep = false;
@@ -201,19 +259,18 @@ int oracle_finish(oracle_state *s) {
         while (!visit.empty()) {
             int64_t u = visit.front();
             visit.pop_front();
-            int32_t ux = tile_x(u), uy = tile_y(u);
             std::vector<int64_t> ns;  /* neighbors(u, delta) in sigma */
+            const int dz_max = s->dims == 3 ? s->delta : 0;
             for (int dx = -s->delta; dx <= s->delta; ++dx)
-                for (int dy = -s->delta; dy <= s->delta; ++dy) {
-                    if (dx == 0 && dy == 0) continue;
-                    if (s->metric == ORACLE_MANHATTAN && std::abs(dx) + std::abs(dy) > s->delta) continue;
-                    int64_t nx = (int64_t)ux + dx, ny = (int64_t)uy + dy;
-                    /* tiles outside the valid index range never exist */
-                    if (nx < -2147483647LL || nx > 2147483646LL) continue;
-                    if (ny < -2147483647LL || ny > 2147483646LL) continue;
-                    int64_t nk = pack((int32_t)nx, (int32_t)ny);
-                    if (sigma.count(nk)) ns.push_back(nk);
-                }
+                for (int dy = -s->delta; dy <= s->delta; ++dy)
+                    for (int dz = -dz_max; dz <= dz_max; ++dz) {
+                        if (dx == 0 && dy == 0 && dz == 0) continue;
+                        if (s->metric == ORACLE_MANHATTAN && std::abs(dx) + std::abs(dy) + std::abs(dz) > s->delta)
+                            continue;
+                        int64_t nk;
+                        if (!neighbour_key(u, dx, dy, dz, s->dims, &nk)) continue;
+                        if (sigma.count(nk)) ns.push_back(nk);
+                    }
             cluster.push_back(u);
             for (int64_t k : ns) {
                 sigma.erase(k);
@@ -228,14 +285,14 @@ int oracle_finish(oracle_state *s) {
     for (const auto &c : clusters) {
         int64_t cid = c[0];
         for (int64_t k : c)
-            if (tile_less(k, cid)) cid = k;
+            if (before(s, k, cid)) cid = k;
         for (int64_t k : c) rows.push_back({k, cid});
         s->cid_of.reserve(s->cid_of.size() + c.size());
         for (int64_t k : c) s->cid_of[k] = cid;
     }
     std::sort(rows.begin(), rows.end(),
-              [](const std::pair<int64_t, int64_t> &a, const std::pair<int64_t, int64_t> &b) {
-                  return tile_less(a.first, b.first);
+              [s](const std::pair<int64_t, int64_t> &a, const std::pair<int64_t, int64_t> &b) {
+                  return before(s, a.first, b.first);
               });
     for (const auto &r : rows) {
         s->kept_key.push_back(r.first);
@@ -259,7 +316,7 @@ void oracle_copy_tiles(const oracle_state *s, int64_t *key, uint64_t *count) {
     std::vector<int64_t> keys;
     keys.reserve(s->acc.size());
     for (const auto &kv : s->acc) keys.push_back(kv.first);
-    std::sort(keys.begin(), keys.end(), tile_less);
+    std::sort(keys.begin(), keys.end(), [s](int64_t a, int64_t b) { return before(s, a, b); });
     for (size_t i = 0; i < keys.size(); ++i) {
         key[i] = keys[i];
         count[i] = s->acc.at(keys[i]);
@@ -282,7 +339,7 @@ int oracle_labels(const oracle_state *s, const double *xy, int64_t n, int64_t *l
     int st = ORACLE_OK;
     for (int64_t i = 0; i < n; ++i) {
         int64_t key;
-        if (!project(xy[2 * i], xy[2 * i + 1], s->scale, &key)) {
+        if (!project_point(xy, i, s->dims, s->scale, &key)) {
             labels[i] = NOISE;
             st = ORACLE_RANGE;
             continue;
@@ -304,7 +361,7 @@ int64_t oracle_point_groups(const oracle_state *s, const double *xy, int64_t n, 
     std::vector<int64_t> rows(n, -1), count(s->kept_key.size(), 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t key;
-        if (!project(xy[2 * i], xy[2 * i + 1], s->scale, &key)) continue;
+        if (!project_point(xy, i, s->dims, s->scale, &key)) continue;
         auto it = row_of.find(key);
         if (it == row_of.end()) continue;
         rows[i] = it->second;
@@ -321,10 +378,10 @@ int64_t oracle_point_groups(const oracle_state *s, const double *xy, int64_t n, 
 }
 
 /* Projection alone, for pinning: keys[i] and ok[i] (1 valid, 0 range error). */
-void oracle_project(const double *xy, int64_t n, double scale, int64_t *keys, uint8_t *ok) {
+void oracle_project(const double *xy, int64_t n, double scale, int64_t *keys, uint8_t *ok, int dims) {
     for (int64_t i = 0; i < n; ++i) {
         int64_t key = 0;
-        bool good = project(xy[2 * i], xy[2 * i + 1], scale, &key);
+        bool good = project_point(xy, i, dims, scale, &key);
         keys[i] = good ? key : 0;
         ok[i] = good ? 1 : 0;
     }
@@ -333,7 +390,7 @@ void oracle_project(const double *xy, int64_t n, double scale, int64_t *keys, ui
 /* Exact counts of a given set of tiles over a point set (one pass), used to
  * check sampled outputs of very large runs one by one. */
 void oracle_count_keys(const double *xy, int64_t n, double scale, const int64_t *keys, int64_t k,
-                       uint64_t *counts) {
+                       uint64_t *counts, int dims) {
     std::unordered_map<int64_t, int64_t> where;
     for (int64_t j = 0; j < k; ++j) {
         where[keys[j]] = j;
@@ -341,7 +398,7 @@ void oracle_count_keys(const double *xy, int64_t n, double scale, const int64_t 
     }
     for (int64_t i = 0; i < n; ++i) {
         int64_t key;
-        if (!project(xy[2 * i], xy[2 * i + 1], scale, &key)) continue;
+        if (!project_point(xy, i, dims, scale, &key)) continue;
         auto it = where.find(key);
         if (it != where.end()) counts[it->second] += 1;
     }

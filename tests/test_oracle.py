@@ -520,3 +520,101 @@ def test_delta_hand_cases():
     assert clusters([(0, 0), (2, 1)], oracle.CHEBYSHEV, 2) == 1
     assert clusters([(0, 0), (2, 1)], oracle.MANHATTAN, 2) == 2
     assert clusters([(0, 0), (2, 1)], oracle.MANHATTAN, 3) == 1
+
+
+# ---------------------------------------------------------------------------
+# Three coordinates (Sect. 3.6, "Generalizing to Higher Dimensions").
+
+def _points3_for_tiles(tiles, scale, rng, max_count=6):
+    xyz = []
+    for t in tiles:
+        for _ in range(rng.randint(1, max_count)):
+            xyz.append(tuple((c + rng.uniform(0.05, 0.95)) / scale for c in t))
+    rng.shuffle(xyz)
+    return np.array(xyz, dtype=np.float64)
+
+
+def _random_tiles3(rng, t, span):
+    out = []
+    for _ in range(t):
+        x0, y0, z0 = (rng.randint(-span, span) for _ in range(3))
+        if rng.random() < 0.6:
+            for _ in range(rng.randint(1, 10)):
+                out.append((x0 + rng.randint(-1, 1), y0 + rng.randint(-1, 1), z0 + rng.randint(-1, 1)))
+        else:
+            out.append((x0, y0, z0))
+    return out
+
+
+def test_3d_counts_match_numpy_unique():
+    g = np.random.default_rng(31)
+    xyz = np.concatenate([g.uniform(-5, 5, (50_000, 3)), g.normal(1.0, 0.02, (30_000, 3))])
+    r, o = oracle.raster(xyz, 2, 3, 2)
+    keys, counts = o.tiles()
+    f = np.floor(xyz * 100.0).astype(np.int64)
+    uk, uc = np.unique(oracle.pack3(f[:, 0], f[:, 1], f[:, 2]), return_counts=True)
+    assert np.array_equal(keys, uk) and np.array_equal(counts, uc.astype(np.uint64))  # integer order is (x, y, z) order
+    assert r.points == xyz.shape[0] and r.n_tiles == len(uk)
+
+
+def test_3d_projection_range():
+    """Each index must lie in [-(2^20 - 1), 2^20 - 2]."""
+    lo, hi = -(2 ** 20 - 1), 2 ** 20 - 2
+    xyz = np.array([[lo + 0.5, 0.5, 0.5], [hi + 0.5, 0.5, 0.5], [lo - 0.5, 0.5, 0.5], [hi + 1.5, 0.5, 0.5],
+                    [0.5, np.nan, 0.5], [0.5, 0.5, -np.inf]])
+    keys, ok = oracle.project(xyz, 1.0)
+    assert ok.tolist() == [True, True, False, False, False, False]
+    x, y, z = oracle.unpack3(keys[:2])
+    assert x.tolist() == [lo, hi] and y.tolist() == [0, 0] and z.tolist() == [0, 0]
+
+
+@pytest.mark.parametrize("metric,full", [(oracle.CHEBYSHEV, 3), (oracle.MANHATTAN, 1)])
+@pytest.mark.parametrize("seed", range(3))
+def test_3d_components_match_scipy_labelling(metric, full, seed):
+    """Chebyshev distance 1 in 3-D is 26-connectivity and Manhattan 1 is
+    6-connectivity: scipy's labelling with the matching structure gives the
+    same components."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = random.Random(500 + seed)
+    xyz = _points3_for_tiles(_random_tiles3(rng, 120, 8), 100.0, rng)
+    tau = 2
+    r, o = oracle.raster(xyz, 2, tau, 1, metric=metric)
+    keys, counts = o.tiles()
+    sig = keys[counts >= tau]
+    c = np.stack(oracle.unpack3(sig), axis=1)
+    c0 = c.min(axis=0)
+    grid = np.zeros(tuple(c.max(axis=0) - c0 + 1), dtype=bool)
+    grid[tuple((c - c0).T)] = True
+    lab, n = ndimage.label(grid, structure=ndimage.generate_binary_structure(3, full))
+    assert r.n_clusters == n
+    comp = lab[tuple((c - c0).T)]
+    by_key = dict(zip(r.key.tolist(), r.cid.tolist()))
+    for k in range(1, n + 1):
+        members = sig[comp == k]
+        cids = {by_key[int(m)] for m in members}
+        assert cids == {int(members.min())}  # id = lexicographically smallest tile = smallest key
+
+
+@pytest.mark.parametrize("metric,delta", [(oracle.MANHATTAN, 2), (oracle.MANHATTAN, 3), (oracle.CHEBYSHEV, 1)])
+@pytest.mark.parametrize("seed", range(3))
+def test_3d_match_brute_force(metric, delta, seed):
+    rng = random.Random(600 + seed)
+    xyz = _points3_for_tiles(_random_tiles3(rng, 60, 10), 100.0, rng)
+    tau, mu = rng.choice([1, 2, 3]), rng.choice([1, 2, 3])
+    r, o = oracle.raster(xyz, 2, tau, mu, metric=metric, delta=delta)
+    keys, counts = o.tiles()
+    bk, bc, bcid, bn = oracle.brute_force(keys, counts, tau, mu, metric=metric, delta=delta, dims=3)
+    assert np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and np.array_equal(r.count, bc)
+    assert r.n_clusters == bn
+
+
+def test_3d_labels_and_groups():
+    rng = random.Random(77)
+    xyz = _points3_for_tiles(_random_tiles3(rng, 80, 6), 100.0, rng)
+    r, lab, o = oracle.raster(xyz, 2, 2, 2, with_labels=True)
+    keys, ok = oracle.project(xyz, 100.0)
+    cid_of = dict(zip(r.key.tolist(), r.cid.tolist()))
+    assert lab.tolist() == [cid_of.get(int(k), int(oracle.NOISE)) for k in keys]
+    rs, idx = o.point_groups(xyz)
+    for i, k in enumerate(r.key.tolist()):
+        assert set(idx[rs[i]:rs[i + 1]].tolist()) == set(np.flatnonzero(keys == k).tolist())

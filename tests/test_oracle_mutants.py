@@ -13,20 +13,23 @@ import oracle
 SRC = os.path.join(os.path.dirname(oracle.__file__), "raster_oracle.cpp")
 
 MUTANTS = {
-    "four_connected": ("if (dx == 0 && dy == 0) continue;",
-                       "if (dx == 0 && dy == 0) continue;\n if (dx != 0 && dy != 0) continue;"),
+    "four_connected": ("if (dx == 0 && dy == 0 && dz == 0) continue;",
+                       "if (dx == 0 && dy == 0 && dz == 0) continue;\n if (dx != 0 && dy != 0) continue;"),
     "strict_tau": ("kv.second >= s->tau", "kv.second > s->tau"),
     "truncate_not_floor": ("std::floor(scaled)", "std::trunc(scaled)"),
     "strict_mu": ("cluster.size() >= s->mu", "cluster.size() > s->mu"),
-    "max_id": ("if (tile_less(k, cid)) cid = k;", "if (tile_less(cid, k)) cid = k;"),
+    "max_id": ("if (before(s, k, cid)) cid = k;", "if (before(s, cid, k)) cid = k;"),
     "transposed_key": ("*key = pack(ix, iy);", "*key = pack(iy, ix);"),
     "single_precision_scale": ("v * scale", "v * (double)(float)scale"),
     "lost_increment": ("it->second += 1;", "it->second += (it->second > 3) ? 0 : 1;"),
     "range_off_by_one": ("f <= 2147483646.0", "f <= 2147483647.0"),
     "group_window_2x1": ("for (int gy = 0; gy <= 1; ++gy)", "for (int gy = 0; gy <= 0; ++gy)"),
     "group_strict_tau": ("if (total >= s->tau) keep = true;", "if (total > s->tau) keep = true;"),
-    "manhattan_strict": ("std::abs(dx) + std::abs(dy) > s->delta", "std::abs(dx) + std::abs(dy) >= s->delta"),
+    "manhattan_strict": ("std::abs(dx) + std::abs(dy) + std::abs(dz) > s->delta",
+                         "std::abs(dx) + std::abs(dy) + std::abs(dz) >= s->delta"),
     "delta_ignored": ("for (int dx = -s->delta; dx <= s->delta; ++dx)", "for (int dx = -1; dx <= 1; ++dx)"),
+    "third_axis_ignored": ("const int dz_max = s->dims == 3 ? s->delta : 0;", "const int dz_max = 0;"),
+    "third_field_shift": ("((iy + BIAS3) << 21)", "((iy + BIAS3) << 20)"),
 }
 
 
@@ -92,6 +95,24 @@ def _pins_pass(lib) -> bool:
         if not (np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and r.n_clusters == bn
                 and r.n_significant == int(sig.sum())):
             return False
+    # three coordinates: counts against numpy, components against scipy (26-connectivity)
+    g = np.random.default_rng(3)
+    xyz = np.concatenate([g.uniform(0, 0.2, (4000, 3)), g.uniform(-1, 1, (3000, 3))])
+    r, o = oracle.raster(xyz, 2, 2, 1, lib=lib)
+    keys, counts = o.tiles()
+    f = np.floor(xyz * 100.0).astype(np.int64)
+    uk, uc = np.unique(oracle.pack3(f[:, 0], f[:, 1], f[:, 2]), return_counts=True)
+    if not (np.array_equal(keys, uk) and np.array_equal(counts, uc.astype(np.uint64))):
+        return False
+    ndimage = pytest.importorskip("scipy.ndimage")
+    sig = uk[uc >= 2]
+    c = np.stack(oracle.unpack3(sig), axis=1)
+    c0 = c.min(axis=0)
+    grid = np.zeros(tuple(c.max(axis=0) - c0 + 1), dtype=bool)
+    grid[tuple((c - c0).T)] = True
+    _, n = ndimage.label(grid, structure=ndimage.generate_binary_structure(3, 3))
+    if r.n_clusters != n:
+        return False
     return True
 
 
