@@ -604,6 +604,38 @@ def run_gpu(args):
                          "phases_ms": ms, "n_significant": resx.n_significant, "n_clusters": resx.n_clusters,
                          "kept_tiles": int(resx.key.numel())}
             rx.close()
+        # three coordinates per point (Sect. 3.6, higher dimensions): 100M points
+        # in 100,000 cubes of side 0.1 plus 10M noise points in [0, 100)^3
+        c3 = gen.CUBES_100M
+        xyz = torch.from_numpy(gen.cubes3(**c3)).to(dev)
+        n3 = xyz.shape[0]
+        lab3 = torch.empty(n3, dtype=torch.int64, device=dev)
+        r3 = R.Raster(1.5, 5, 4, dims=3)
+        times = {"contract": [], "agglomerate": [], "labels": []}
+        for rep in range(4):
+            e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+            e0.record(stream)
+            r3.reset()
+            r3.contract(xyz)
+            e1.record(stream)
+            res3 = r3.agglomerate(copy=False, raw=True)
+            e2.record(stream)
+            r3.point_labels(xyz, out=lab3)
+            e3.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                times["contract"].append(e0.elapsed_time(e1))
+                times["agglomerate"].append(e1.elapsed_time(e2))
+                times["labels"].append(e2.elapsed_time(e3))
+        ms = {k: statistics.mean(v) for k, v in times.items()}
+        step_ms = max_over_ranks(sum(ms.values()), dev)
+        ext["three_coordinates"] = {
+            "value": whole_job_rate(world, n3, step_ms / 1e3), "unit": "points/s", "ms_per_step": step_ms,
+            "phases_ms": ms, "workload": dict(c3, precision=1.5, tau=5, mu=4, dims=3),
+            "n_distinct": res3.n_distinct, "n_significant": res3.n_significant, "n_clusters": res3.n_clusters,
+            "contraction_frac": (24 * n3 + 12 * res3.n_distinct) / (ms["contract"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
+        r3.close()
+        del xyz, lab3
         line["extensions"] = ext
 
     # e2e: host buffers through the C ABI, copies inside the timed region

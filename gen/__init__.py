@@ -187,3 +187,20 @@ def serve_requests(rate_per_s: float, duration_s: float, seed: int = 5, lo: int 
 def chunk_bounds(n: int, chunks: int) -> list[tuple[int, int]]:
     """Split [0, n) into ``chunks`` nearly equal contiguous ranges."""
     return [(n * c // chunks, n * (c + 1) // chunks) for c in range(chunks)]
+
+
+# ---------------------------------------------------------------------------
+# Three-coordinate points: cubes of uniform points (centres uniform in the
+# canvas cube) plus uniform noise, shuffled.  numpy's seeded generator; the
+# same arrays on any machine.
+
+CUBES_100M = dict(n_clusters=100_000, per=900, side=0.1, canvas=100.0, noise=10_000_000, seed=21)
+
+
+def cubes3(n_clusters: int, per: int, side: float, canvas: float, noise: int, seed: int) -> np.ndarray:
+    g = np.random.default_rng(seed)
+    centres = g.uniform(0.0, canvas, (n_clusters, 3))
+    out = np.empty((n_clusters * per + noise, 3), dtype=np.float64)
+    out[:n_clusters * per] = (centres[:, None, :] + g.uniform(-side / 2, side / 2, (n_clusters, per, 3))).reshape(-1, 3)
+    out[n_clusters * per:] = g.uniform(0.0, canvas, (noise, 3))
+    return out[g.permutation(out.shape[0])]

@@ -94,18 +94,29 @@ int raster_create(double precision, uint32_t tau, uint32_t mu, raster_handle **o
  *   groups   0 or 1.  1 adds the post-processing step of Sect. 3.6
  *            ("disadvantageous grid layouts", Fig. 4): every occupied tile of
  *            a group of 2 x 2 tiles holding at least tau points together is
- *            significant too (raster_clusters.n_significant counts them). */
+ *            significant too (raster_clusters.n_significant counts them).
+ *   dims     coordinates per point: 2 (or 0), or 3 (the generalisation to
+ *            higher dimensions of Sect. 3.6).  With 3, every point array of
+ *            the handle is n x 3 float64, 8-byte aligned; each tile index
+ *            must lie in [-(2^20 - 1), 2^20 - 2] (else RASTER_E_RANGE) and
+ *            key = (ix + 2^20) << 42 | (iy + 2^20) << 21 | (iz + 2^20), so
+ *            integer key order is (ix, iy, iz) order and cluster ids are the
+ *            smallest key; neighbours are taken over all three axes
+ *            (Chebyshev 1: the 26 surrounding tiles); groups must be 0. */
 typedef struct {
     double precision;
     uint32_t tau, mu;
     uint32_t metric;
     uint32_t delta;
     uint32_t groups;
+    uint32_t dims;
 } raster_params;
 
 /* Create a handle with the parameters above (Alg. 1 inputs prec, tau, delta,
  * mu).  RASTER_E_ARG for an unknown metric, delta outside 1..RASTER_MAX_DELTA,
- * groups other than 0/1, or any argument raster_create refuses.  Every other
+ * groups other than 0/1, dims other than 0/2/3, groups with dims 3, a
+ * neighbourhood of more than 40 forward offsets (three coordinates allow
+ * Chebyshev 1 and Manhattan up to 3), or any argument raster_create refuses.  Every other
  * call works on such a handle as on one from raster_create; the batched,
  * served and fixed-capacity entry points use Chebyshev distance 1 only. */
 int raster_create_ex(const raster_params *params, raster_handle **out);
@@ -117,9 +128,11 @@ int raster_reserve(raster_handle *h, int64_t n_tiles);
 
 /* Contraction of one chunk (Alg. 1 first loop; chunked processing, Sect. 3.6).
  * xy: DEVICE pointer to n points as interleaved float64 pairs (x0,y0,x1,y1,..),
- *   16-byte aligned; caller-owned and must stay valid until the stream work
- *   completes.  n >= 0.  Callable any number of times; counts accumulate.
- * Work is enqueued on `stream`; the call synchronises once per 2^28 points
+ *   16-byte aligned (triples x,y,z, 8-byte aligned, for a handle created
+ *   with dims = 3; the same holds for every point array below); caller-owned
+ *   and must stay valid until the stream work completes.  n >= 0.  Callable
+ *   any number of times; counts accumulate.
+ * Work is enqueued on `stream`; the call synchronises once per 2^30 points
  * to read the table's tile count (and grows the table when needed), so xy
  * may be released when it returns.  The total number of points per handle
  * must stay below 2^32. */

@@ -19,7 +19,8 @@ import torch
 from . import _native
 from ._native import CHEBYSHEV, MANHATTAN, NOISE, RasterError, check, lib
 
-__all__ = ["Raster", "Result", "RasterError", "NOISE", "CHEBYSHEV", "MANHATTAN", "lib", "build", "pack", "unpack"]
+__all__ = ["Raster", "Result", "RasterError", "NOISE", "CHEBYSHEV", "MANHATTAN", "lib", "build", "pack", "unpack",
+           "pack3", "unpack3"]
 
 
 def build(force: bool = False) -> str:
@@ -33,6 +34,18 @@ def pack(ix: torch.Tensor, iy: torch.Tensor) -> torch.Tensor:
 
 def unpack(key: torch.Tensor):
     return key >> 32, (key & 0xFFFFFFFF).to(torch.int32).to(torch.int64)
+
+
+BIAS3 = 1 << 20  # three coordinates: 21-bit index fields, each offset by 2^20
+
+
+def pack3(ix: torch.Tensor, iy: torch.Tensor, iz: torch.Tensor) -> torch.Tensor:
+    ix, iy, iz = (t.to(torch.int64) for t in (ix, iy, iz))
+    return ((ix + BIAS3) << 42) | ((iy + BIAS3) << 21) | (iz + BIAS3)
+
+
+def unpack3(key: torch.Tensor):
+    return tuple(((key >> sh) & 0x1FFFFF) - BIAS3 for sh in (42, 21, 0))
 
 
 class _DeviceArray:
@@ -62,16 +75,20 @@ class Result:
     n_significant: int
     n_points: int
     status: int
+    dims: int = 2  # coordinates per point of the handle that produced it
 
     def sorted(self) -> "Result":
-        """Rows in (ix, iy) order (the library's row order is unspecified)."""
+        """Rows in (ix, iy[, iz]) order (the library's row order is unspecified)."""
         if self.key.numel() == 0:
             return self
-        ix, iy = unpack(self.key)
-        order = torch.argsort(iy, stable=True)
-        order = order[torch.argsort(ix[order], stable=True)]
+        if self.dims == 3:  # integer key order is (ix, iy, iz) order
+            order = torch.argsort(self.key, stable=True)
+        else:
+            ix, iy = unpack(self.key)
+            order = torch.argsort(iy, stable=True)
+            order = order[torch.argsort(ix[order], stable=True)]
         return Result(self.key[order], self.count[order], self.cid[order], self.n_clusters, self.n_distinct,
-                      self.n_significant, self.n_points, self.status)
+                      self.n_significant, self.n_points, self.status, self.dims)
 
 
 def _stream_ptr(stream) -> ctypes.c_void_p:
@@ -80,24 +97,27 @@ def _stream_ptr(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _check_points(xy: torch.Tensor, where: str):
-    if not (xy.is_cuda and xy.dtype == torch.float64 and xy.dim() == 2 and xy.shape[1] == 2 and xy.is_contiguous()):
-        raise ValueError(f"{where}: expected a contiguous (n, 2) float64 CUDA tensor")
+def _check_points(xy: torch.Tensor, where: str, dims: int = 2):
+    if not (xy.is_cuda and xy.dtype == torch.float64 and xy.dim() == 2 and xy.shape[1] == dims and xy.is_contiguous()):
+        raise ValueError(f"{where}: expected a contiguous (n, {dims}) float64 CUDA tensor")
 
 
 class Raster:
     """One RASTER problem (precision, tau, mu) with a device-resident tile table."""
 
     def __init__(self, precision: float, tau: int, mu: int, metric: int = CHEBYSHEV, delta: int = 1,
-                 groups: bool = False):
+                 groups: bool = False, dims: int = 2):
         """metric/delta: neighbors(u, delta) (Sect. 3.2; default Chebyshev 1);
-        groups: the 2 x 2 group rule of Sect. 3.6."""
+        groups: the 2 x 2 group rule of Sect. 3.6; dims: coordinates per
+        point, 2 or 3 (Sect. 3.6, higher dimensions)."""
         self._L = lib()
+        self.dims = int(dims)
         h = ctypes.c_void_p()
-        if metric == CHEBYSHEV and delta == 1 and not groups:
+        if metric == CHEBYSHEV and delta == 1 and not groups and dims == 2:
             check(self._L.raster_create(float(precision), int(tau), int(mu), ctypes.byref(h)), "raster_create")
         else:
-            p = _native.Params(float(precision), int(tau), int(mu), int(metric), int(delta), 1 if groups else 0)
+            p = _native.Params(float(precision), int(tau), int(mu), int(metric), int(delta), 1 if groups else 0,
+                               int(dims))
             check(self._L.raster_create_ex(ctypes.byref(p), ctypes.byref(h)), "raster_create_ex")
         self._h = h
         self.precision, self.tau, self.mu = precision, tau, mu
@@ -139,13 +159,13 @@ class Raster:
         check(self._L.raster_reserve(self._h, int(n_tiles)), "raster_reserve")
 
     def contract(self, xy: torch.Tensor, stream=None):
-        _check_points(xy, "contract")
+        _check_points(xy, "contract", self.dims)
         check(self._L.raster_contract(self._h, ctypes.c_void_p(xy.data_ptr()), xy.shape[0], _stream_ptr(stream)),
               "raster_contract")
 
     def contract_host(self, xy, stream=None):
         """xy: host (n, 2) float64 (pinned torch tensor or numpy array)."""
-        ptr, n = _host_ptr(xy)
+        ptr, n = _host_ptr(xy, cols=self.dims)
         check(self._L.raster_contract_host(self._h, ctypes.c_void_p(ptr), n, _stream_ptr(stream)),
               "raster_contract_host")
 
@@ -165,10 +185,10 @@ class Raster:
             key, cid = key.clone(), cid.clone()
         if not raw:
             cnt = cnt.to(torch.int64) & 0xFFFFFFFF
-        return Result(key, cnt, cid, out.n_clusters, out.n_distinct, out.n_significant, out.n_points, st)
+        return Result(key, cnt, cid, out.n_clusters, out.n_distinct, out.n_significant, out.n_points, st, self.dims)
 
     def point_labels(self, xy: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        _check_points(xy, "point_labels")
+        _check_points(xy, "point_labels", self.dims)
         if out is None:
             out = torch.empty(xy.shape[0], dtype=torch.int64, device=xy.device)
         assert out.is_cuda and out.dtype == torch.int64 and out.is_contiguous() and out.numel() == xy.shape[0]
@@ -178,7 +198,7 @@ class Raster:
         return out
 
     def point_labels_host(self, xy, out=None, stream=None):
-        ptr, n = _host_ptr(xy)
+        ptr, n = _host_ptr(xy, cols=self.dims)
         if out is None:
             out = torch.empty(n, dtype=torch.int64)
         optr, on = _host_ptr(out, cols=None)
@@ -192,7 +212,7 @@ class Raster:
         the indices of the points of each kept tile, rows in the order of the
         last agglomerate() result (n_tiles = its number of rows).  `out` may
         give (row_start, point_index) buffers of n_tiles+1 and n entries."""
-        _check_points(xy, "point_groups")
+        _check_points(xy, "point_groups", self.dims)
         n = xy.shape[0]
         if out is None:
             out = (torch.empty(n_tiles + 1, dtype=torch.int64, device=xy.device),

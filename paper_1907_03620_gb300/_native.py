@@ -35,7 +35,8 @@ class RasterError(RuntimeError):
 class Params(ctypes.Structure):
     """raster_params"""
     _fields_ = [("precision", ctypes.c_double), ("tau", ctypes.c_uint32), ("mu", ctypes.c_uint32),
-                ("metric", ctypes.c_uint32), ("delta", ctypes.c_uint32), ("groups", ctypes.c_uint32)]
+                ("metric", ctypes.c_uint32), ("delta", ctypes.c_uint32), ("groups", ctypes.c_uint32),
+                ("dims", ctypes.c_uint32)]
 
 
 class Instance(ctypes.Structure):

@@ -56,6 +56,28 @@ __device__ __forceinline__ unsigned long long key_of_order(unsigned long long o)
     return o ^ 0x8000000080000000ull;
 }
 
+// Three coordinates (the generalisation of Sect. 3.6 to higher dimensions):
+// each index in [-(2^20 - 1), 2^20 - 2], stored plus 2^20 in a 21-bit field,
+// x in the top field, so that integer key order is (x, y, z) order and the top
+// bit is clear (no key equals kEmptyKey or kInvalidKey).
+constexpr long long kBias3 = 1ll << 20;
+constexpr int kMin3 = -(int)(kBias3 - 1), kMax3 = (int)(kBias3 - 2);
+__device__ __forceinline__ unsigned long long pack_key3(long long ix, long long iy, long long iz) {
+    return ((unsigned long long)(ix + kBias3) << 42) | ((unsigned long long)(iy + kBias3) << 21) |
+           (unsigned long long)(iz + kBias3);
+}
+__device__ __forceinline__ int key3(unsigned long long k, int axis) {
+    return (int)((k >> (42 - 21 * axis)) & 0x1FFFFFull) - (int)kBias3;
+}
+
+template <bool WIDE>
+__device__ __forceinline__ unsigned long long project_point3(double x, double y, double z, const ProjParams& pp) {
+    int ix, iy, iz;
+    const bool ok = project_coord<WIDE>(x, pp, &ix) & project_coord<WIDE>(y, pp, &iy) & project_coord<WIDE>(z, pp, &iz);
+    if (!ok || ix < kMin3 || ix > kMax3 || iy < kMin3 || iy > kMax3 || iz < kMin3 || iz > kMax3) return kInvalidKey;
+    return pack_key3(ix, iy, iz);
+}
+
 template <bool WIDE>
 __device__ __forceinline__ unsigned long long project_point(double x, double y, const ProjParams& pp) {
     int ix, iy;

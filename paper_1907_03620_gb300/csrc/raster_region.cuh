@@ -29,6 +29,7 @@ struct RegionTable {
     unsigned int regions;
     unsigned int region_bits;
     unsigned int max_probe;
+    int dims;  // coordinates of the keys: 2, or 3 (spatial blocks of 8 x 8 x 8 tiles)
 };
 
 __device__ __forceinline__ unsigned int block_hash(unsigned long long key) {
@@ -43,8 +44,21 @@ __device__ __forceinline__ unsigned int block_hash(unsigned long long key) {
     return h;
 }
 
+__device__ __forceinline__ unsigned int block_hash3(unsigned long long key) {
+    const unsigned int bx = (unsigned int)(key3(key, 0) >> 3), by = (unsigned int)(key3(key, 1) >> 3);
+    const unsigned int bz = (unsigned int)(key3(key, 2) >> 3);
+    unsigned int h = bx * 0x9E3779B1u + by * 0x85EBCA77u + bz * 0xC2B2AE3Du;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return h;
+}
+
 __device__ __forceinline__ unsigned int region_of(unsigned long long key, const RegionTable& t) {
-    return (unsigned int)(((unsigned long long)block_hash(key) * t.regions) >> 32);
+    const unsigned int h = t.dims == 3 ? block_hash3(key) : block_hash(key);
+    return (unsigned int)(((unsigned long long)h * t.regions) >> 32);
 }
 
 __device__ __forceinline__ unsigned long long home_slot(unsigned long long key, const RegionTable& t) {

@@ -109,8 +109,33 @@ __device__ __forceinline__ void overflow_append(bool want, unsigned long long ke
     ovf_cnt[pos] = c;
 }
 
-template <bool WIDE>
-__global__ void __launch_bounds__(kBlock, 4) k_part(const double2* __restrict__ xy, long long n, ProjParams pp,
+// Point i of an array of DIMS coordinates per point (two: one 16-byte load),
+// and its tile key, or kInvalidKey.
+template <int DIMS>
+struct PointIn {
+    double c[DIMS];
+};
+template <int DIMS>
+__device__ __forceinline__ PointIn<DIMS> load_point(const double* __restrict__ xy, long long i) {
+    PointIn<DIMS> p;
+    if (DIMS == 2) {
+        const double2 v = __ldcs(reinterpret_cast<const double2*>(xy) + i);
+        p.c[0] = v.x;
+        p.c[1] = v.y;
+    } else {
+#pragma unroll
+        for (int a = 0; a < DIMS; ++a) p.c[a] = __ldcs(xy + DIMS * i + a);
+    }
+    return p;
+}
+template <bool WIDE, int DIMS>
+__device__ __forceinline__ unsigned long long project_in(const PointIn<DIMS>& p, const ProjParams& pp) {
+    if (DIMS == 2) return project_point<WIDE>(p.c[0], p.c[1], pp);
+    return project_point3<WIDE>(p.c[0], p.c[1], p.c[DIMS - 1], pp);
+}
+
+template <bool WIDE, int DIMS>
+__global__ void __launch_bounds__(kBlock, 4) k_part(const double* __restrict__ xy, long long n, ProjParams pp,
                                                 RegionTable t, unsigned long long* __restrict__ stage,
                                                 unsigned long long seg_cap, unsigned int* __restrict__ cursor,
                                                 unsigned long long* ovf_key, unsigned int* ovf_cnt,
@@ -127,11 +152,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double2* __restrict__ 
     for (long long t0 = (long long)blockIdx.x * kPartTile; t0 < n; t0 += (long long)gridDim.x * kPartTile) {
         for (int r = threadIdx.x; r < R; r += kBlock) s_fill[r] = 0u;
         __syncthreads();
-        double2 p[kPartPer];
+        // two coordinates: all of the thread's loads in flight before projecting;
+        // three: loaded where projected (registers)
+        PointIn<DIMS> p[DIMS == 2 ? kPartPer : 1];
+        if (DIMS == 2) {
 #pragma unroll
-        for (int k = 0; k < kPartPer; ++k) {
-            const long long idx = t0 + k * kBlock + threadIdx.x;
-            if (idx < n) p[k] = __ldcs(xy + idx);
+            for (int k = 0; k < kPartPer; ++k) {
+                const long long idx = t0 + k * kBlock + threadIdx.x;
+                if (idx < n) p[DIMS == 2 ? k : 0] = load_point<DIMS>(xy, idx);
+            }
         }
         unsigned long long key[kPartPer];
         unsigned int meta[kPartPer];
@@ -141,7 +170,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double2* __restrict__ 
             meta[k] = 0xFFFFFFFFu;
             key[k] = 0ull;
             if (idx < n) {
-                key[k] = project_point<WIDE>(p[k].x, p[k].y, pp);
+                key[k] = project_in<WIDE, DIMS>(DIMS == 2 ? p[DIMS == 2 ? k : 0] : load_point<DIMS>(xy, idx), pp);
                 if (key[k] == kInvalidKey) {
                     st |= kStRange;
                 } else {
@@ -598,8 +627,10 @@ __device__ __forceinline__ long long next_chunk(unsigned long long* work, long l
 constexpr int kMaxFwd = ((2 * RASTER_MAX_DELTA + 1) * (2 * RASTER_MAX_DELTA + 1) - 1) / 2;
 struct NbrSet {
     int n;
+    int dims;
     signed char dx[kMaxFwd];
     signed char dy[kMaxFwd];
+    signed char dz[kMaxFwd];
 };
 
 // One thread per (significant tile, forward neighbour); a tile's lookups and
@@ -610,22 +641,23 @@ struct NbrSet {
 template <bool GENERAL>
 __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
                                                 const unsigned long long* __restrict__ sig_key, RegionTable t,
-                                                NbrSet nbr, int* parent, unsigned long long* work,
-                                                unsigned int* d_status) {
+                                                const NbrSet* __restrict__ nbr, int nfwd, int dims, int* parent,
+                                                unsigned long long* work, unsigned int* d_status) {
     __shared__ long long s_chunk;
-    const int F = GENERAL ? nbr.n : 4;
+    const int F = GENERAL ? nfwd : 4;
     const long long SF = (long long)F * (long long)*d_nsig;
     unsigned int st = 0;
     for (long long w0 = next_chunk(work, &s_chunk); w0 < SF; w0 = next_chunk(work, &s_chunk)) {
         const long long w = w0 + threadIdx.x;
         if (w >= SF) continue;
         long long i;
-        int dx, dy;
+        int dx, dy, dz = 0;
         if (GENERAL) {
             i = w / F;
             const int q = (int)(w - i * F);
-            dx = nbr.dx[q];
-            dy = nbr.dy[q];
+            dx = __ldg(&nbr->dx[q]);
+            dy = __ldg(&nbr->dy[q]);
+            dz = __ldg(&nbr->dz[q]);
         } else {
             i = w >> 2;
             const int q = (int)(w & 3);
@@ -633,10 +665,17 @@ __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsi
             dy = q < 3 ? q - 1 : 1;
         }
         const unsigned long long key = sig_key[i];
-        const long long nx = (long long)key_x(key) + dx;
-        const long long ny = (long long)key_y(key) + dy;
-        if (nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll) continue;
-        const unsigned long long nk = pack_key((int)nx, (int)ny);
+        unsigned long long nk;
+        if (GENERAL && dims == 3) {
+            const int nx = key3(key, 0) + dx, ny = key3(key, 1) + dy, nz = key3(key, 2) + dz;
+            if (nx < kMin3 || nx > kMax3 || ny < kMin3 || ny > kMax3 || nz < kMin3 || nz > kMax3) continue;
+            nk = pack_key3(nx, ny, nz);
+        } else {
+            const long long nx = (long long)key_x(key) + dx;
+            const long long ny = (long long)key_y(key) + dy;
+            if (nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll) continue;
+            nk = pack_key((int)nx, (int)ny);
+        }
         const Slot nb = rt_get(t, nk);
         if (nb.key != nk || nb.aux == kAuxNone) continue;
         if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
@@ -694,10 +733,23 @@ __global__ void __launch_bounds__(kBlock) k_flatten(const unsigned long long* d_
     }
 }
 
+// Order of keys as unsigned integers: (x, y) order after flipping both sign
+// bits of a two-coordinate key; a three-coordinate key is in (x, y, z) order
+// as it stands.
+constexpr unsigned long long kOrderXor2 = 0x8000000080000000ull, kOrderXor3 = 0ull;
+
+// A kept tile's label code: offsets to its cluster-id tile for two
+// coordinates, the escape to its result row for three.
+__device__ __forceinline__ unsigned int label_code_d(unsigned long long key, unsigned long long cid, unsigned int row,
+                                                     int dims) {
+    return dims == 3 ? (0x80000000u | row) : label_code(key, cid, row);
+}
+
 __global__ void __launch_bounds__(kBlock) k_stats(const unsigned long long* d_nsig,
                                                  const unsigned long long* __restrict__ sig_key,
                                                  const int* __restrict__ parent, unsigned int* csize,
-                                                 unsigned long long* cmin, unsigned long long* work) {
+                                                 unsigned long long* cmin, unsigned long long* work,
+                                                 unsigned long long order_xor) {
     __shared__ long long s_chunk;
     const long long S = (long long)*d_nsig;
     for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
@@ -705,7 +757,7 @@ __global__ void __launch_bounds__(kBlock) k_stats(const unsigned long long* d_ns
         if (i < S) {
             const int r = parent[i];
             atomicAdd(&csize[r], 1u);
-            atomicMin(&cmin[r], order_of(sig_key[i]));
+            atomicMin(&cmin[r], sig_key[i] ^ order_xor);
         }
     }
 }
@@ -719,7 +771,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsi
                                                 Slot* tab, unsigned long long* out_key, unsigned int* out_cnt,
                                                 unsigned long long* out_cid, unsigned int* out_slot,
                                                 unsigned long long* d_nkept, unsigned long long* d_nclusters,
-                                                unsigned long long* work) {
+                                                unsigned long long* work, unsigned long long order_xor, int dims) {
     __shared__ unsigned int scratch[33];
     __shared__ unsigned long long s_base;
     __shared__ long long s_chunk;
@@ -734,7 +786,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsi
             r = parent[i];
             keep = csize[r] >= mu;
             key = sig_key[i];
-            cid = key_of_order(cmin[r]);
+            cid = cmin[r] ^ order_xor;
             if (keep && r == (int)i) ++clusters;
         }
         unsigned int total;
@@ -749,7 +801,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsi
                 out_cnt[row] = sig_cnt[i];
                 out_cid[row] = cid;
                 out_slot[row] = sig_slot[i];
-                code = label_code(key, cid, (unsigned int)row);
+                code = label_code_d(key, cid, (unsigned int)row, dims);
             }
             tab[sig_slot[i]].aux = code;
         }
@@ -759,15 +811,14 @@ __global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsi
     if ((threadIdx.x & 31) == 0 && clusters) atomicAdd(d_nclusters, (unsigned long long)clusters);
 }
 
-template <bool WIDE>
-__global__ void k_labels(const double2* __restrict__ xy, long long n, ProjParams pp, RegionTable t, unsigned int tau,
+template <bool WIDE, int DIMS>
+__global__ void k_labels(const double* __restrict__ xy, long long n, ProjParams pp, RegionTable t, unsigned int tau,
                          const long long* __restrict__ cid_rows, long long* __restrict__ labels,
                          unsigned int* d_status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned int st = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double2 p = __ldcs(xy + i);
-        const unsigned long long key = project_point<WIDE>(p.x, p.y, pp);
+        const unsigned long long key = project_in<WIDE, DIMS>(load_point<DIMS>(xy, i), pp);
         long long lab = (long long)kEmptyKey;
         if (key == kInvalidKey) {
             st |= kStRange;
@@ -791,21 +842,20 @@ __global__ void k_aux_rows(const unsigned long long* d_nkept, const unsigned int
 
 __global__ void k_aux_codes(const unsigned long long* d_nkept, const unsigned int* __restrict__ out_slot,
                             const unsigned long long* __restrict__ out_key,
-                            const unsigned long long* __restrict__ out_cid, Slot* tab) {
+                            const unsigned long long* __restrict__ out_cid, Slot* tab, int dims) {
     const long long K = (long long)*d_nkept;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < K; r += stride)
-        tab[out_slot[r]].aux = label_code(out_key[r], out_cid[r], (unsigned int)r);
+        tab[out_slot[r]].aux = label_code_d(out_key[r], out_cid[r], (unsigned int)r, dims);
 }
 
-template <bool WIDE>
-__global__ void k_group_count(const double2* __restrict__ xy, long long n, ProjParams pp, RegionTable t,
+template <bool WIDE, int DIMS>
+__global__ void k_group_count(const double* __restrict__ xy, long long n, ProjParams pp, RegionTable t,
                               unsigned int tau, unsigned int* row_count, int* point_row, unsigned int* d_status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned int st = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double2 p = __ldcs(xy + i);
-        const unsigned long long key = project_point<WIDE>(p.x, p.y, pp);
+        const unsigned long long key = project_in<WIDE, DIMS>(load_point<DIMS>(xy, i), pp);
         int row = -1;
         if (key == kInvalidKey) {
             st |= kStRange;
@@ -923,8 +973,10 @@ struct raster_handle {
     unsigned int tau = 1, mu = 1;
     // neighbors(u, delta): forward offsets; `general` unless Chebyshev 1
     NbrSet nbr{};
+    NbrSet* d_nbr = nullptr;  // device copy, read by the hook kernel
     bool general = false;
     bool groups = false;  // the 2 x 2 group rule of Sect. 3.6
+    int dims = 2;         // coordinates per point: 2 or 3
     ProjParams pp{};
     bool wide = false;
     cudaStream_t stream = nullptr;
@@ -1036,6 +1088,7 @@ RegionTable table_of(const raster_handle* h) {
     t.regions = h->regions;
     t.region_bits = h->region_bits;
     t.max_probe = max_probe_for(h->cap);
+    t.dims = h->dims;
     return t;
 }
 
@@ -1091,6 +1144,7 @@ int grow_table(raster_handle* h, unsigned int regions, unsigned int bits) {
     t.cap = new_cap;
     t.regions = regions;
     t.region_bits = bits;
+    t.dims = h->dims;
     t.max_probe = max_probe_for(new_cap);
     if (h->tab && h->cap && !h->fresh) {
         static int grid = grid_for((const void*)k_rehash, kBlock);
@@ -1218,21 +1272,26 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
     const unsigned long long seg = h->stage_cap / h->regions;
     RegionTable t = table_of(h);
     const size_t smem = part_smem(h->regions);
-    static bool attr_set = false;
-    if (!attr_set) {
-        RCHECK(h, cudaFuncSetAttribute(k_part<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr_set = true;
+    const void* part = h->dims == 3 ? (const void*)k_part<WIDE, 3> : (const void*)k_part<WIDE, 2>;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[h->dims - 2]) {
+        RCHECK(h, cudaFuncSetAttribute(part, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set[h->dims - 2] = true;
     }
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_part<WIDE>, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, part, kBlock, smem);
     const long long tiles = (n + kPartTile - 1) / kPartTile;
     const int g1 = (int)std::max<long long>(1, std::min<long long>((long long)sms * std::max(per_sm, 1), tiles));
     RCHECK(h, cudaMemsetAsync(h->cursor, 0, sizeof(unsigned int) * h->regions, h->stream));
     RCHECK(h, cudaMemsetAsync(h->d_ctr + 5, 0, sizeof(unsigned long long), h->stream));
-    k_part<WIDE><<<g1, kBlock, smem, h->stream>>>(reinterpret_cast<const double2*>(xy), n, h->pp, t, h->stage_keys,
-                                                 seg, h->cursor, h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_status);
+    if (h->dims == 3)
+        k_part<WIDE, 3><<<g1, kBlock, smem, h->stream>>>(xy, n, h->pp, t, h->stage_keys, seg, h->cursor, h->ovf_key,
+                                                         h->ovf_cnt, h->d_ctr + 5, h->d_status);
+    else
+        k_part<WIDE, 2><<<g1, kBlock, smem, h->stream>>>(xy, n, h->pp, t, h->stage_keys, seg, h->cursor, h->ovf_key,
+                                                         h->ovf_cnt, h->d_ctr + 5, h->d_status);
     k_region_items<<<1, kBlock, 0, h->stream>>>(h->cursor, (int)h->regions, seg, h->item_start);
     // pass 2: whole buckets in shared memory, unless the round is much smaller
     // than the table (and the table is live), where rewriting every bucket
@@ -1313,7 +1372,8 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
 int contract_device(raster_handle* h, const double* xy, long long n) {
     for (long long off = 0; off < n; off += kRoundPoints) {
         const long long m = std::min(n - off, kRoundPoints);
-        const int rc = h->wide ? contract_round<true>(h, xy + 2 * off, m) : contract_round<false>(h, xy + 2 * off, m);
+        const double* p = xy + (long long)h->dims * off;
+        const int rc = h->wide ? contract_round<true>(h, p, m) : contract_round<false>(h, p, m);
         if (rc) return rc;
     }
     return RASTER_OK;
@@ -1342,7 +1402,7 @@ int ensure_stage(raster_handle* h) {
     const long long pts = 64ll << 20;  // 64M points = 1 GiB of xy per buffer
     RCHECK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
     for (int b = 0; b < 2; ++b) {
-        RCHECK(h, cudaMalloc(&h->stage_xy[b], (size_t)pts * 16));
+        RCHECK(h, cudaMalloc(&h->stage_xy[b], (size_t)pts * 8 * h->dims));
         RCHECK(h, cudaMalloc(&h->stage_lab[b], (size_t)pts * 8));
         RCHECK(h, cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming));
         RCHECK(h, cudaEventCreateWithFlags(&h->ev_done[b], cudaEventDisableTiming));
@@ -1351,7 +1411,22 @@ int ensure_stage(raster_handle* h) {
     return RASTER_OK;
 }
 
-bool misaligned(const void* p) { return ((uintptr_t)p & 15u) != 0; }
+template <bool WIDE, int DIMS>
+void launch_labels(raster_handle* h, const double* xy, long long n, int64_t* labels) {
+    static int grid = grid_for((const void*)k_labels<WIDE, DIMS>, kBlock);
+    k_labels<WIDE, DIMS><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
+        xy, n, h->pp, table_of(h), h->tau, reinterpret_cast<const long long*>(h->out_cid),
+        reinterpret_cast<long long*>(labels), h->d_status);
+}
+
+template <bool WIDE, int DIMS>
+void launch_group_count(raster_handle* h, const double* xy, long long n) {
+    static int grid = grid_for((const void*)k_group_count<WIDE, DIMS>, kBlock);
+    k_group_count<WIDE, DIMS><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
+        xy, n, h->pp, table_of(h), h->tau, h->row_count, h->point_row, h->d_status);
+}
+
+bool misaligned(const void* p, int dims = 2) { return ((uintptr_t)p & (dims == 3 ? 7u : 15u)) != 0; }
 
 }  // namespace
 
@@ -1419,6 +1494,7 @@ int raster_create(double precision, uint32_t tau, uint32_t mu, raster_handle** o
     p.metric = RASTER_CHEBYSHEV;
     p.delta = 1;
     p.groups = 0;
+    p.dims = 2;
     return raster_create_ex(&p, out);
 }
 
@@ -1429,6 +1505,9 @@ int raster_create_ex(const raster_params* params, raster_handle** out) {
     if (tau == 0 || mu == 0 || !std::isfinite(precision)) return RASTER_E_ARG;
     if (params->metric != RASTER_CHEBYSHEV && params->metric != RASTER_MANHATTAN) return RASTER_E_ARG;
     if (params->delta < 1 || params->delta > RASTER_MAX_DELTA || params->groups > 1) return RASTER_E_ARG;
+    const int dims = params->dims == 0 ? 2 : (int)params->dims;
+    if (dims != 2 && dims != 3) return RASTER_E_ARG;
+    if (dims == 3 && params->groups) return RASTER_E_ARG;  // the group rule is defined for 2 x 2 tiles
     *out = nullptr;
     raster_handle* h = new (std::nothrow) raster_handle();
     if (!h) return RASTER_E_OOM;
@@ -1437,19 +1516,28 @@ int raster_create_ex(const raster_params* params, raster_handle** out) {
     h->tau = tau;
     h->mu = mu;
     h->groups = params->groups != 0;
-    h->general = !(params->metric == RASTER_CHEBYSHEV && params->delta == 1);
+    h->dims = dims;
+    h->general = dims == 3 || !(params->metric == RASTER_CHEBYSHEV && params->delta == 1);
     {
-        const int d = (int)params->delta;
+        // forward half of the ball: the first nonzero offset is positive
+        const int d = (int)params->delta, dz_max = dims == 3 ? d : 0;
         int n = 0;
         for (int dx = 0; dx <= d; ++dx)
-            for (int dy = -d; dy <= d; ++dy) {
-                if (dx == 0 && dy <= 0) continue;  // forward half only
-                if (params->metric == RASTER_MANHATTAN && dx + std::abs(dy) > d) continue;
-                h->nbr.dx[n] = (signed char)dx;
-                h->nbr.dy[n] = (signed char)dy;
-                ++n;
-            }
+            for (int dy = -d; dy <= d; ++dy)
+                for (int dz = -dz_max; dz <= dz_max; ++dz) {
+                    if (dx == 0 && (dy < 0 || (dy == 0 && dz <= 0))) continue;
+                    if (params->metric == RASTER_MANHATTAN && dx + std::abs(dy) + std::abs(dz) > d) continue;
+                    if (n == kMaxFwd) {
+                        delete h;
+                        return RASTER_E_ARG;  // neighbourhood larger than the kernels take
+                    }
+                    h->nbr.dx[n] = (signed char)dx;
+                    h->nbr.dy[n] = (signed char)dy;
+                    h->nbr.dz[n] = (signed char)dz;
+                    ++n;
+                }
         h->nbr.n = n;
+        h->nbr.dims = dims;
     }
     if (make_proj_params(h->scale, &h->pp, &h->wide) != RASTER_OK) {
         delete h;
@@ -1461,6 +1549,8 @@ int raster_create_ex(const raster_params* params, raster_handle** out) {
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctr, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_nbr, sizeof(NbrSet));
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_nbr, &h->nbr, sizeof(NbrSet), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         raster_destroy(h);
         return e == cudaErrorMemoryAllocation ? RASTER_E_OOM : RASTER_E_CUDA;
@@ -1489,7 +1579,7 @@ int raster_reserve(raster_handle* h, int64_t n_tiles) {
 }
 
 int raster_contract(raster_handle* h, const double* xy, int64_t n, void* stream) {
-    if (!h || n < 0 || (n > 0 && (!xy || misaligned(xy)))) return RASTER_E_ARG;
+    if (!h || n < 0 || (n > 0 && (!xy || misaligned(xy, h->dims)))) return RASTER_E_ARG;
     if (hard_error(h->status)) return h->status;
     if (h->points + n > 0xFFFFFFFFll) return RASTER_E_ARG;  // per-tile counts are 32-bit
     h->stream = (cudaStream_t)stream;
@@ -1517,7 +1607,8 @@ int raster_contract_host(raster_handle* h, const double* xy_host, int64_t n, voi
         const long long off = c * h->stage_points;
         const long long m = std::min(n - off, h->stage_points);
         RCHECK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_done[b], 0));
-        RCHECK(h, cudaMemcpyAsync(h->stage_xy[b], xy_host + 2 * off, (size_t)m * 16, cudaMemcpyHostToDevice,
+        RCHECK(h, cudaMemcpyAsync(h->stage_xy[b], xy_host + (long long)h->dims * off, (size_t)m * 8 * h->dims,
+                                  cudaMemcpyHostToDevice,
                                   h->copy_stream));
         RCHECK(h, cudaEventRecord(h->ev_copied[b], h->copy_stream));
         return RASTER_OK;
@@ -1578,17 +1669,21 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     RCHECK(h, cudaMemsetAsync(h->d_work, 0, 8 * sizeof(unsigned long long), s));
     const long long F = h->general ? h->nbr.n : 4;  // forward neighbours per significant tile
     if (h->general)
-        k_hook<true><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->nbr,
-                                                                           h->parent, h->d_work + 1, h->d_status);
+        k_hook<true><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->d_nbr,
+                                                                           h->nbr.n, h->dims, h->parent,
+                                                                           h->d_work + 1, h->d_status);
     else
-        k_hook<false><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->nbr,
-                                                                            h->parent, h->d_work + 1, h->d_status);
+        k_hook<false><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->d_nbr,
+                                                                            4, 2, h->parent, h->d_work + 1,
+                                                                            h->d_status);
     k_flatten<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->d_work + 2);
+    const unsigned long long order_xor = h->dims == 3 ? kOrderXor3 : kOrderXor2;
     k_stats<<<std::min(g_stat, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->parent, h->csize, h->cmin,
-                                                     h->d_work + 3);
+                                                     h->d_work + 3, order_xor);
     k_emit<<<std::min(g_emit, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->sig_cnt, h->sig_slot, h->parent, h->csize,
                                                     h->cmin, h->mu, h->tab, h->out_key, h->out_cnt, h->out_cid,
-                                                    h->out_slot, h->d_ctr + 2, h->d_ctr + 3, h->d_work + 4);
+                                                    h->out_slot, h->d_ctr + 2, h->d_ctr + 3, h->d_work + 4, order_xor,
+                                                    h->dims);
     note_launch(5);
     RCHECK(h, cudaGetLastError());
     rc = read_counters(h);
@@ -1608,22 +1703,15 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
 }
 
 int raster_point_labels(raster_handle* h, const double* xy, int64_t n, int64_t* labels, void* stream) {
-    if (!h || n < 0 || (n > 0 && (!xy || !labels || misaligned(xy)))) return RASTER_E_ARG;
+    if (!h || n < 0 || (n > 0 && (!xy || !labels || misaligned(xy, h->dims)))) return RASTER_E_ARG;
     if (hard_error(h->status)) return h->status;
     if (h->state != raster_handle::kAgglomerated) return RASTER_E_STATE;
     h->stream = (cudaStream_t)stream;
     if (n == 0) return RASTER_OK;
-    if (h->wide) {
-        static int grid = grid_for((const void*)k_labels<true>, kBlock);
-        k_labels<true><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
-            reinterpret_cast<const double2*>(xy), n, h->pp, table_of(h), h->tau,
-            reinterpret_cast<const long long*>(h->out_cid), reinterpret_cast<long long*>(labels), h->d_status);
-    } else {
-        static int grid = grid_for((const void*)k_labels<false>, kBlock);
-        k_labels<false><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
-            reinterpret_cast<const double2*>(xy), n, h->pp, table_of(h), h->tau,
-            reinterpret_cast<const long long*>(h->out_cid), reinterpret_cast<long long*>(labels), h->d_status);
-    }
+    if (h->dims == 3)
+        h->wide ? launch_labels<true, 3>(h, xy, n, labels) : launch_labels<false, 3>(h, xy, n, labels);
+    else
+        h->wide ? launch_labels<true, 2>(h, xy, n, labels) : launch_labels<false, 2>(h, xy, n, labels);
     note_launch();
     RCHECK(h, cudaGetLastError());
     return RASTER_OK;
@@ -1645,7 +1733,8 @@ int raster_point_labels_host(raster_handle* h, const double* xy_host, int64_t n,
         const int b = c & 1;
         const long long m = std::min(n - off, h->stage_points);
         RCHECK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_done[b], 0));
-        RCHECK(h, cudaMemcpyAsync(h->stage_xy[b], xy_host + 2 * off, (size_t)m * 16, cudaMemcpyHostToDevice,
+        RCHECK(h, cudaMemcpyAsync(h->stage_xy[b], xy_host + (long long)h->dims * off, (size_t)m * 8 * h->dims,
+                                  cudaMemcpyHostToDevice,
                                   h->copy_stream));
         RCHECK(h, cudaEventRecord(h->ev_copied[b], h->copy_stream));
         RCHECK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
@@ -1662,7 +1751,7 @@ int raster_point_labels_host(raster_handle* h, const double* xy_host, int64_t n,
 
 int raster_point_groups(raster_handle* h, const double* xy, int64_t n, int64_t* row_start, int64_t* point_index,
                         int64_t capacity, int64_t* n_grouped, void* stream) {
-    if (!h || n < 0 || !n_grouped || !row_start || capacity < 0 || (n > 0 && (!xy || misaligned(xy))))
+    if (!h || n < 0 || !n_grouped || !row_start || capacity < 0 || (n > 0 && (!xy || misaligned(xy, h->dims))))
         return RASTER_E_ARG;
     if (hard_error(h->status)) return h->status;
     if (h->state != raster_handle::kAgglomerated) return RASTER_E_STATE;
@@ -1697,21 +1786,17 @@ int raster_point_groups(raster_handle* h, const double* xy, int64_t n, int64_t* 
     RCHECK(h, cudaMemsetAsync(h->row_count, 0, sizeof(unsigned int) * (size_t)(K + 1), s));
     k_aux_rows<<<gk, kBlock, 0, s>>>(d_nkept, h->out_slot, h->tab);
     if (n > 0) {
-        const int gp = (int)std::min<long long>(grid_for((const void*)k_group_count<false>, kBlock),
-                                                (n + kBlock - 1) / kBlock);
-        if (h->wide)
-            k_group_count<true><<<gp, kBlock, 0, s>>>(reinterpret_cast<const double2*>(xy), n, h->pp, table_of(h),
-                                                     h->tau, h->row_count, h->point_row, h->d_status);
+        if (h->dims == 3)
+            h->wide ? launch_group_count<true, 3>(h, xy, n) : launch_group_count<false, 3>(h, xy, n);
         else
-            k_group_count<false><<<gp, kBlock, 0, s>>>(reinterpret_cast<const double2*>(xy), n, h->pp, table_of(h),
-                                                      h->tau, h->row_count, h->point_row, h->d_status);
+            h->wide ? launch_group_count<true, 2>(h, xy, n) : launch_group_count<false, 2>(h, xy, n);
     }
     const int gs = (int)std::max<long long>(1, std::min<long long>(1024, (K + kScanTile - 1) / kScanTile));
     long long* rs = reinterpret_cast<long long*>(row_start);
     k_scan_tiles<<<gs, kBlock, 0, s>>>(d_nkept, h->row_count, rs, h->scan_sums);
     k_scan_sums<<<1, kBlock, 0, s>>>(d_nkept, h->scan_sums, rs);
     k_scan_add<<<gk, kBlock, 0, s>>>(d_nkept, h->scan_sums, rs);
-    k_aux_codes<<<gk, kBlock, 0, s>>>(d_nkept, h->out_slot, h->out_key, h->out_cid, h->tab);
+    k_aux_codes<<<gk, kBlock, 0, s>>>(d_nkept, h->out_slot, h->out_key, h->out_cid, h->tab, h->dims);
     note_launch(n > 0 ? 6 : 5);
     RCHECK(h, cudaGetLastError());
     long long m = 0;
@@ -1794,7 +1879,7 @@ int raster_destroy(raster_handle* h) {
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
                     h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
                     h->ovf_cnt, h->d_work, h->out_slot, h->point_row, h->row_count, h->scan_sums,
-                    h->stage2,  h->bcursor};
+                    h->stage2,  h->bcursor, h->d_nbr};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);

@@ -40,3 +40,10 @@ def test_batched_instances_follow_recipe():
         assert w.precision in (1, 2, 3) and w.tau in (3, 5, 8) and w.mu in (2, 4)
         assert w.cluster_points == w.n - int(w.n * 0.10)
         assert w.clusters == max(1, w.n // 500)
+
+
+def test_cubes3_deterministic_and_in_range():
+    a = gen.cubes3(50, 40, 0.1, 5.0, 300, 9)
+    b = gen.cubes3(50, 40, 0.1, 5.0, 300, 9)
+    assert a.shape == (50 * 40 + 300, 3) and np.array_equal(a, b)
+    assert a.min() >= -0.05 and a.max() <= 5.05
