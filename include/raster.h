@@ -162,6 +162,23 @@ int raster_point_labels(raster_handle *h, const double *xy, int64_t n, int64_t *
 int raster_point_labels_host(raster_handle *h, const double *xy_host, int64_t n, int64_t *labels_host,
                              void *stream);
 
+/* The whole method on HOST points in one call (Alg. 1 and the RASTER* labels,
+ * Sect. 4.1): contraction of the n points at HOST xy_host (layout as for
+ * raster_contract, added to whatever the handle holds), agglomeration into
+ * *out (as raster_agglomerate), and the label of each of the n points into
+ * HOST labels_host (int64[n], as raster_point_labels).  The points are copied
+ * to the device once, in chunks, each chunk's first contraction pass running
+ * while later chunks are still being copied, and they stay on the device (a
+ * buffer owned by the handle, reused by later calls, freed by
+ * raster_destroy) for the label pass; labels return chunk by chunk behind
+ * the label kernels.  If that buffer cannot be allocated the call copies the
+ * points twice instead (raster_contract_host, raster_agglomerate,
+ * raster_point_labels_host).  Pinned host memory makes the copies
+ * asynchronous.  Synchronous; returns what raster_agglomerate returns, or
+ * the first error. */
+int raster_cluster_host(raster_handle *h, const double *xy_host, int64_t n, int64_t *labels_host,
+                        raster_clusters *out, void *stream);
+
 /* RASTER' output (Sect. 3.4; clusters as sets of points, Fig. 2d): the points
  * of every kept tile, grouped by result row.  Requires a preceding
  * raster_agglomerate with no contract since; rows follow the order of that

@@ -187,6 +187,34 @@ class Raster:
             cnt = cnt.to(torch.int64) & 0xFFFFFFFF
         return Result(key, cnt, cid, out.n_clusters, out.n_distinct, out.n_significant, out.n_points, st, self.dims)
 
+    def _result(self, out, st, copy: bool, raw: bool) -> Result:
+        n = out.n_tiles
+        key = _view(out.key, n, torch.int64, self.device)
+        cnt = _view(out.count, n, torch.int32, self.device)
+        cid = _view(out.cid, n, torch.int64, self.device)
+        if copy:
+            key, cid = key.clone(), cid.clone()
+        if not raw:
+            cnt = cnt.to(torch.int64) & 0xFFFFFFFF
+        return Result(key, cnt, cid, out.n_clusters, out.n_distinct, out.n_significant, out.n_points, st, self.dims)
+
+    def cluster_host(self, xy, out=None, copy: bool = True, allow_range_error: bool = False, raw: bool = False,
+                     stream=None):
+        """The whole method on host points in one call: contraction (one copy of
+        the points to the device), agglomeration, and the label of every point
+        back in host memory.  Returns (Result, labels)."""
+        ptr, n = _host_ptr(xy, cols=self.dims)
+        if out is None:
+            out = torch.empty(n, dtype=torch.int64, pin_memory=torch.cuda.is_available())
+        optr, on = _host_ptr(out, cols=None)
+        assert on == n
+        res = _native.Clusters()
+        st = self._L.raster_cluster_host(self._h, ctypes.c_void_p(ptr), n, ctypes.c_void_p(optr), ctypes.byref(res),
+                                         _stream_ptr(stream))
+        if st != _native.OK and not (allow_range_error and st == _native.E_RANGE):
+            raise RasterError(st, "raster_cluster_host")
+        return self._result(res, st, copy, raw), out
+
     def point_labels(self, xy: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         _check_points(xy, "point_labels", self.dims)
         if out is None:

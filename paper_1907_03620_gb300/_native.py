@@ -88,6 +88,7 @@ def _declare(L):
         "raster_agglomerate": (ci, [vp, ctypes.POINTER(Clusters)]),
         "raster_point_labels": (ci, [vp, vp, i64, vp, vp]),
         "raster_point_labels_host": (ci, [vp, vp, i64, vp, vp]),
+        "raster_cluster_host": (ci, [vp, vp, i64, vp, ctypes.POINTER(Clusters), vp]),
         "raster_export_tiles": (ci, [vp, vp, vp, i64, ctypes.POINTER(i64)]),
         "raster_point_groups": (ci, [vp, vp, i64, vp, vp, i64, ctypes.POINTER(i64), vp]),
         "raster_reset": (ci, [vp, vp]),

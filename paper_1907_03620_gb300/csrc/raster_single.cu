@@ -977,6 +977,10 @@ struct raster_handle {
     bool general = false;
     bool groups = false;  // the 2 x 2 group rule of Sect. 3.6
     int dims = 2;         // coordinates per point: 2 or 3
+    bool round_grew = false;  // the table was grown at the start of the current round
+    // device copy of the points of raster_cluster_host (kept for the labels)
+    double* res_xy = nullptr;
+    size_t res_bytes = 0;
     ProjParams pp{};
     bool wide = false;
     cudaStream_t stream = nullptr;
@@ -1238,6 +1242,7 @@ int ensure_staging(raster_handle* h, long long n) {
 }
 
 constexpr long long kRoundPoints = 1ll << 30;    // points per contraction round
+constexpr long long kClusterChunk = 16ll << 20;  // points per copy of raster_cluster_host
 constexpr double kNewLimit = 0.8;                // no new tiles beyond this load within a round
 constexpr unsigned int kInsertProbe = 1024;      // global insert: longer probe sequences go to the overflow list
 constexpr double kBucketRound = 0.25;            // rounds of fewer points per table slot insert globally
@@ -1247,16 +1252,16 @@ constexpr double kPreGrow = 4.0;                 // grow before a round whose es
 // One contraction round of n points: pass 1, item prefix, pass 1b, pass 2
 // (all asynchronous), then one synchronisation to read the table's tile count
 // and the overflow counts.  If keys overflowed or the table is too full, grow
-// it and re-insert the overflow list.
-template <bool WIDE>
-int contract_round(raster_handle* h, const double* xy, long long n) {
+// it and re-insert the overflow list.  Pass 1 may run chunk by chunk (as host
+// copies arrive): round_begin, round_part for each chunk, round_finish.
+int round_begin(raster_handle* h, long long n) {
     // A round far larger than the table (the first call into the initial
     // table, say) grows it first: a full bucket would pass its remaining keys
     // to the overflow list one block at a time.  D + n/2 estimates the tiles
     // after the round; a table that turns out far too large is rebuilt
-    // smaller below.
+    // smaller in round_finish.
     int rc;
-    bool grew = false;
+    h->round_grew = false;
     const double est = (double)h->d_bound + 0.5 * (double)n;
     if (est > kPreGrow * kMaxLoad * (double)h->cap) {
         unsigned int regions, bits;
@@ -1264,11 +1269,20 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
         if (((unsigned long long)regions << bits) <= (1ull << 32)) {
             rc = grow_table(h, regions, bits);
             if (rc) return rc;
-            grew = true;
+            h->round_grew = true;
         }
     }
     rc = ensure_staging(h, n);
     if (rc) return rc;
+    RCHECK(h, cudaMemsetAsync(h->cursor, 0, sizeof(unsigned int) * h->regions, h->stream));
+    RCHECK(h, cudaMemsetAsync(h->d_ctr + 5, 0, sizeof(unsigned long long), h->stream));
+    return RASTER_OK;
+}
+
+// Pass 1 over m points of the round (appends to the staging segments).
+template <bool WIDE>
+int round_part(raster_handle* h, const double* xy, long long m) {
+    if (m <= 0) return RASTER_OK;
     const unsigned long long seg = h->stage_cap / h->regions;
     RegionTable t = table_of(h);
     const size_t smem = part_smem(h->regions);
@@ -1282,16 +1296,24 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, part, kBlock, smem);
-    const long long tiles = (n + kPartTile - 1) / kPartTile;
+    const long long tiles = (m + kPartTile - 1) / kPartTile;
     const int g1 = (int)std::max<long long>(1, std::min<long long>((long long)sms * std::max(per_sm, 1), tiles));
-    RCHECK(h, cudaMemsetAsync(h->cursor, 0, sizeof(unsigned int) * h->regions, h->stream));
-    RCHECK(h, cudaMemsetAsync(h->d_ctr + 5, 0, sizeof(unsigned long long), h->stream));
     if (h->dims == 3)
-        k_part<WIDE, 3><<<g1, kBlock, smem, h->stream>>>(xy, n, h->pp, t, h->stage_keys, seg, h->cursor, h->ovf_key,
+        k_part<WIDE, 3><<<g1, kBlock, smem, h->stream>>>(xy, m, h->pp, t, h->stage_keys, seg, h->cursor, h->ovf_key,
                                                          h->ovf_cnt, h->d_ctr + 5, h->d_status);
     else
-        k_part<WIDE, 2><<<g1, kBlock, smem, h->stream>>>(xy, n, h->pp, t, h->stage_keys, seg, h->cursor, h->ovf_key,
+        k_part<WIDE, 2><<<g1, kBlock, smem, h->stream>>>(xy, m, h->pp, t, h->stage_keys, seg, h->cursor, h->ovf_key,
                                                          h->ovf_cnt, h->d_ctr + 5, h->d_status);
+    note_launch();
+    RCHECK(h, cudaGetLastError());
+    return RASTER_OK;
+}
+
+int round_finish(raster_handle* h, long long n) {
+    int rc;
+    const bool grew_before = h->round_grew;
+    const unsigned long long seg = h->stage_cap / h->regions;
+    RegionTable t = table_of(h);
     k_region_items<<<1, kBlock, 0, h->stream>>>(h->cursor, (int)h->regions, seg, h->item_start);
     // pass 2: whole buckets in shared memory, unless the round is much smaller
     // than the table (and the table is live), where rewriting every bucket
@@ -1306,7 +1328,7 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
         k_insert<<<g2, kBlock, 0, h->stream>>>(ti, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
                                               (unsigned long long)((double)h->cap * kNewLimit), h->d_ctr,
                                               h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work);
-        note_launch(3);
+        note_launch(2);
         RCHECK(h, cudaGetLastError());
     } else {
         // pass 1b: by bucket within each region
@@ -1331,13 +1353,14 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
                                        (unsigned int)(kNewLimit * kBucketSlots), h->d_ctr, h->d_ctr + 6, h->ovf_key,
                                        h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
         h->fresh = false;  // every bucket has been written
-        note_launch(4);
+        note_launch(3);
         RCHECK(h, cudaGetLastError());
     }
     rc = read_counters(h);
     if (rc) return rc;
     const unsigned long long D = h->h_ctr[0], ovf = h->h_ctr[5], full = h->h_ctr[6];
     // D + ovf bounds the tile count; a bucket that refused new tiles needs room too
+    bool grew = grew_before;
     if ((double)(D + ovf) > kMaxLoad * (double)h->cap || full > 0) {
         const double need = std::max((double)(D + ovf) / kGrowLoad, 1.5 * (double)h->cap);
         unsigned int regions, bits;
@@ -1367,6 +1390,15 @@ int contract_round(raster_handle* h, const double* xy, long long n) {
     }
     h->d_bound = (long long)h->h_ctr[0];
     return RASTER_OK;
+}
+
+template <bool WIDE>
+int contract_round(raster_handle* h, const double* xy, long long n) {
+    int rc = round_begin(h, n);
+    if (rc) return rc;
+    rc = round_part<WIDE>(h, xy, n);
+    if (rc) return rc;
+    return round_finish(h, n);
 }
 
 int contract_device(raster_handle* h, const double* xy, long long n) {
@@ -1840,6 +1872,79 @@ int raster_export_tiles(raster_handle* h, int64_t* key, uint32_t* count, int64_t
     return RASTER_OK;
 }
 
+int raster_cluster_host(raster_handle* h, const double* xy_host, int64_t n, int64_t* labels_host,
+                        raster_clusters* out, void* stream) {
+    if (!h || !out || n < 0 || (n > 0 && (!xy_host || !labels_host))) return RASTER_E_ARG;
+    if (hard_error(h->status)) return h->status;
+    if (h->points + n > 0xFFFFFFFFll) return RASTER_E_ARG;
+    h->stream = (cudaStream_t)stream;
+    h->state = raster_handle::kContracting;
+    int rc = ensure_stage(h);
+    if (rc) return rc;
+    const size_t bytes = (size_t)n * 8 * (size_t)h->dims;
+    if (bytes > h->res_bytes) {
+        RCHECK(h, cudaStreamSynchronize(h->stream));
+        if (h->res_xy) cudaFree(h->res_xy);
+        h->res_xy = nullptr;
+        h->res_bytes = 0;
+        if (cudaMalloc(&h->res_xy, bytes) != cudaSuccess) {
+            // no room to keep the points: copy them twice instead
+            cudaGetLastError();
+            h->res_xy = nullptr;
+            rc = raster_contract_host(h, xy_host, n, stream);
+            if (rc) return rc;
+            rc = raster_agglomerate(h, out);
+            if (hard_error(rc)) return rc;
+            const int rl = raster_point_labels_host(h, xy_host, n, labels_host, stream);
+            return rl ? rl : rc;
+        }
+        h->res_bytes = bytes;
+    }
+    h->points += n;
+    // contraction: rounds of at most kRoundPoints; within a round, pass 1 runs
+    // on each chunk as soon as its copy has landed, while later copies proceed
+    const int dims = h->dims;
+    for (long long r0 = 0; r0 < n; r0 += kRoundPoints) {
+        const long long mr = std::min(n - r0, kRoundPoints);
+        rc = round_begin(h, mr);
+        if (rc) return rc;
+        for (long long c0 = 0, c = 0; c0 < mr; c0 += kClusterChunk, ++c) {
+            const int b = (int)(c & 1);
+            const long long m = std::min(mr - c0, kClusterChunk);
+            const long long off = (r0 + c0) * dims;
+            RCHECK(h, cudaMemcpyAsync(h->res_xy + off, xy_host + off, (size_t)m * 8 * dims, cudaMemcpyHostToDevice,
+                                      h->copy_stream));
+            RCHECK(h, cudaEventRecord(h->ev_copied[b], h->copy_stream));
+            RCHECK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
+            rc = h->wide ? round_part<true>(h, h->res_xy + off, m) : round_part<false>(h, h->res_xy + off, m);
+            if (rc) return rc;
+        }
+        rc = round_finish(h, mr);
+        if (rc) return rc;
+    }
+    rc = raster_agglomerate(h, out);
+    if (hard_error(rc)) return rc;
+    // labels of the resident points, copied back chunk by chunk behind the kernels
+    RCHECK(h, cudaEventRecord(h->ev_done[0], h->copy_stream));
+    RCHECK(h, cudaEventRecord(h->ev_done[1], h->copy_stream));
+    for (long long c0 = 0, c = 0; c0 < n; c0 += kClusterChunk, ++c) {
+        const int b = (int)(c & 1);
+        const long long m = std::min(n - c0, kClusterChunk);
+        RCHECK(h, cudaStreamWaitEvent(h->stream, h->ev_done[b], 0));  // the buffer's previous copy is done
+        const int rl = raster_point_labels(h, h->res_xy + c0 * dims, m, reinterpret_cast<int64_t*>(h->stage_lab[b]),
+                                           stream);
+        if (rl) return rl;
+        RCHECK(h, cudaEventRecord(h->ev_copied[b], h->stream));
+        RCHECK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_copied[b], 0));
+        RCHECK(h, cudaMemcpyAsync(labels_host + c0, h->stage_lab[b], (size_t)m * 8, cudaMemcpyDeviceToHost,
+                                  h->copy_stream));
+        RCHECK(h, cudaEventRecord(h->ev_done[b], h->copy_stream));
+    }
+    RCHECK(h, cudaStreamSynchronize(h->copy_stream));
+    RCHECK(h, cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
 int raster_reset(raster_handle* h, void* stream) {
     if (!h) return RASTER_E_ARG;
     h->stream = (cudaStream_t)stream;
@@ -1879,7 +1984,7 @@ int raster_destroy(raster_handle* h) {
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
                     h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
                     h->ovf_cnt, h->d_work, h->out_slot, h->point_row, h->row_count, h->scan_sums,
-                    h->stage2,  h->bcursor, h->d_nbr};
+                    h->stage2,  h->bcursor, h->d_nbr, h->res_xy};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
