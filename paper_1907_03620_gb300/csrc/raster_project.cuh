@@ -12,6 +12,11 @@ struct ProjParams {
     int d0;                    // 1075 - s_exp: v*s = P * 2^-(d0 - e) for v of biased exponent e
     int top;                   // 52 + s_bits: P = significand(v) * s_odd has top or top+1 bits
     double scale;              // s itself, for the rare FP64 path
+    // narrow path (s_bits <= 10): the rounding half-ulp of P for top and for
+    // top+1 bits, the bound 2^top between them, and the largest D whose
+    // product is still a normal double
+    unsigned long long half_lo, half_hi, thr;
+    int dmax;
 };
 
 // Rare path: the definition itself on the FP64 pipe.
@@ -33,7 +38,10 @@ static __device__ __noinline__ bool project_coord_fp64(double v, double scale, i
 // which is one add of a bias before the shift: (P + bias) >> D.  The first
 // gives the tile of a positive coordinate, minus the second that of a negative
 // one.  NARROW (s_odd below 2^10, every integer precision 0..4) keeps P below
-// 2^63; otherwise the 128-bit product is rounded explicitly.
+// 2^63; otherwise the 128-bit product is rounded explicitly.  For a negative
+// coordinate NARROW computes F' = (P - half - 1) >> D, so that ceil = F' + 1
+// and the tile -(F' + 1) = ~F': both signs take the bias half ^ m and give
+// q ^ m with m = 0 or all ones, and share the range bound q <= 2^31 - 2.
 template <bool WIDE>
 __device__ __forceinline__ bool project_coord(double v, const ProjParams& pp, int* out) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -50,18 +58,15 @@ __device__ __forceinline__ bool project_coord(double v, const ProjParams& pp, in
     unsigned long long q;
     if (!WIDE) {
         const unsigned long long P = mx * (unsigned long long)(unsigned int)pp.s_odd;  // < 2^63 (s_odd < 2^10)
-        const int D = pp.d0 - (int)e;                 // v*s = P * 2^-D
-        if (D <= 0) return false;                     // |v*s| >= 2^52
-        const int t = pp.top + (int)((P >> pp.top) != 0ull);  // bit length of P
-        if (D > t) {                                  // |v*s| < 1/2
-            if (D > t + 1021) return project_coord_fp64(v, pp.scale, out);  // subnormal product
-            q = neg ? 1ull : 0ull;
-        } else {
-            const int r = t - 53;                     // 0..10
-            const unsigned long long half = (r > 0) ? (1ull << (r - 1)) : 0ull;
-            const unsigned long long bias = neg ? ((1ull << D) - 1ull - half) : half;
-            q = (P + bias) >> D;                      // D <= t <= 63: no overflow
-        }
+        const int D = pp.d0 - (int)e;                                                 // v*s = P * 2^-D
+        if (D <= 0) return false;                                                     // |v*s| >= 2^52
+        if (D > pp.dmax) return project_coord_fp64(v, pp.scale, out);  // product below the normal range
+        const unsigned long long half = P >= pp.thr ? pp.half_hi : pp.half_lo;
+        const unsigned long long m = neg ? ~0ull : 0ull;
+        const unsigned long long q = (P + (half ^ m)) >> min(D, 63);  // P + bias < 2^63: a shift of 63 gives 0
+        if (q > 2147483646ull) return false;
+        *out = (int)((unsigned int)q ^ (unsigned int)m);
+        return true;
     } else {
         const unsigned long long lo = mx * pp.s_odd;
         const unsigned long long hi = __umul64hi(mx, pp.s_odd);

@@ -249,7 +249,11 @@ __device__ __forceinline__ int find_region(const long long* __restrict__ start, 
 // Pass 1b of contraction: counting-sort each region's staged keys by bucket
 // (the 2^kBucketBits-slot unit of pass 2) into per-bucket segments of a second
 // staging buffer.  Work items are kInsertItem keys of one region; keys beyond
-// a bucket segment's capacity go to the overflow list.
+// a bucket segment's capacity go to the overflow list.  A block claims its
+// next item and starts copying that item's keys to shared memory (cp.async)
+// before sorting the current one, so the claim, the region lookup and the
+// loads of one item overlap the work on the previous.
+constexpr size_t kBucketSmem = (size_t)kInsertItem * (2 * 8 + 2);  // two key buffers + bucket per key
 __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsigned long long* __restrict__ stage,
                                                   unsigned long long seg_cap, const unsigned int* __restrict__ cursor,
                                                   const long long* __restrict__ item_start, int regions,
@@ -257,26 +261,60 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
                                                   unsigned int* __restrict__ bcursor, unsigned long long* ovf_key,
                                                   unsigned int* ovf_cnt, unsigned long long* ovf_n,
                                                   unsigned long long* work) {
-    __shared__ unsigned long long s_sorted[kInsertItem];
-    __shared__ unsigned short s_b[kInsertItem];
+    extern __shared__ __align__(16) unsigned char smem_b[];
+    unsigned long long* s_in = reinterpret_cast<unsigned long long*>(smem_b);        // 2 x kInsertItem keys
+    unsigned short* s_b = reinterpret_cast<unsigned short*>(s_in + 2 * kInsertItem); // kInsertItem
     __shared__ unsigned int s_fill[kBlock], s_start[kBlock], s_gbase[kBlock];
     __shared__ unsigned int scratch[33];
-    __shared__ long long s_it;
+    __shared__ long long s_it[2];
+    __shared__ int s_r[2];
+    __shared__ unsigned long long s_k0[2], s_k1[2];
     const int bb = (int)t.region_bits - kBucketBits;  // buckets per region: 2^bb <= kBlock
     const int NB = 1 << bb;
     const unsigned int local_mask = (1u << t.region_bits) - 1u;
     const long long total = item_start[regions];
+    // claim an item for buffer q and start copying its keys there (one group)
+    auto claim = [&](int q) {
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(work, 1ull);
+            s_it[q] = it;
+            if (it < total) {
+                const int r = find_region(item_start, regions, it);
+                const unsigned long long cnt = min((unsigned long long)cursor[r], seg_cap);
+                const unsigned long long k0 = (unsigned long long)(it - item_start[r]) * kInsertItem;
+                s_r[q] = r;
+                s_k0[q] = k0;
+                s_k1[q] = min(k0 + kInsertItem, cnt);
+            }
+        }
+        __syncthreads();
+        if (s_it[q] < total) {
+            const unsigned long long k0 = s_k0[q], k1 = s_k1[q];
+            const unsigned long long* seg = stage + (unsigned long long)s_r[q] * seg_cap;
+#pragma unroll
+            for (int k = 0; k < (int)(kInsertItem / kBlock); ++k) {
+                const unsigned long long j = k0 + (unsigned long long)(k * kBlock + threadIdx.x);
+                if (j < k1) {
+                    const unsigned int dst = (unsigned int)__cvta_generic_to_shared(
+                        s_in + (size_t)q * kInsertItem + k * kBlock + threadIdx.x);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(seg + j) : "memory");
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    int q = 0;
+    claim(0);
     for (;;) {
-        if (threadIdx.x == 0) s_it = (long long)atomicAdd(work, 1ull);
+        claim(q ^ 1);  // the next item's keys copy while this one is sorted
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
         if (threadIdx.x < NB) s_fill[threadIdx.x] = 0u;
         __syncthreads();
-        const long long it = s_it;
+        const long long it = s_it[q];
         if (it >= total) break;
-        const int r = find_region(item_start, regions, it);
-        const unsigned long long cnt = min((unsigned long long)cursor[r], seg_cap);
-        const unsigned long long k0 = (unsigned long long)(it - item_start[r]) * kInsertItem;
-        const unsigned long long k1 = min(k0 + kInsertItem, cnt);
-        const unsigned long long* seg = stage + (unsigned long long)r * seg_cap;
+        const int r = s_r[q];
+        const unsigned long long k0 = s_k0[q], k1 = s_k1[q];
+        unsigned long long* s_cur = s_in + (size_t)q * kInsertItem;  // this item's keys, then its sorted keys
         unsigned long long key[kInsertItem / kBlock];
         unsigned int meta[kInsertItem / kBlock];
 #pragma unroll
@@ -285,12 +323,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
             meta[k] = 0xFFFFFFFFu;
             key[k] = 0ull;
             if (j < k1) {
-                key[k] = __ldcs(seg + j);
+                key[k] = s_cur[k * kBlock + threadIdx.x];
                 const unsigned int b = (tile_hash(key[k]) & local_mask) >> kBucketBits;
                 meta[k] = (b << 12) | atomicAdd(&s_fill[b], 1u);
             }
         }
-        __syncthreads();
+        __syncthreads();  // also: every key of s_cur is in registers
         const unsigned int n_items = block_excl_scan_bins(s_fill, NB, s_start, scratch);
         const unsigned long long g0 = (unsigned long long)r << bb;  // first bucket of region r
         if (threadIdx.x < NB && s_fill[threadIdx.x])
@@ -300,7 +338,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
             if (meta[k] != 0xFFFFFFFFu) {
                 const unsigned int b = meta[k] >> 12;
                 const unsigned int pos = s_start[b] + (meta[k] & 0xFFFu);
-                s_sorted[pos] = key[k];
+                s_cur[pos] = key[k];
                 s_b[pos] = (unsigned short)b;
             }
         }
@@ -310,7 +348,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
             unsigned long long k = 0;
             bool spill = false;
             if (j < n_items) {
-                k = s_sorted[j];
+                k = s_cur[j];
                 const unsigned int b = s_b[j];
                 const unsigned long long pos = (unsigned long long)s_gbase[b] + (j - s_start[b]);
                 if (pos < seg2)
@@ -321,7 +359,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
             overflow_append(spill, k, 1u, ovf_key, ovf_cnt, ovf_n);
         }
         __syncthreads();
+        q ^= 1;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Add one point to `key` in a bucket held in shared memory (linear probing
@@ -1336,8 +1376,13 @@ int round_finish(raster_handle* h, long long n) {
         const unsigned long long seg2 = (h->stage2_cap / n_buckets) & ~1ull;
         RCHECK(h, cudaMemsetAsync(h->bcursor, 0, sizeof(unsigned int) * n_buckets, h->stream));
         RCHECK(h, cudaMemsetAsync(h->d_work, 0, 2 * sizeof(unsigned long long), h->stream));
-        static int gb = grid_for((const void*)k_bucket, kBlock);
-        k_bucket<<<gb, kBlock, 0, h->stream>>>(t, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
+        static bool bkattr = false;
+        if (!bkattr) {
+            RCHECK(h, cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBucketSmem));
+            bkattr = true;
+        }
+        static int gb = grid_for((const void*)k_bucket, kBlock, kBucketSmem);
+        k_bucket<<<gb, kBlock, kBucketSmem, h->stream>>>(t, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
                                               h->stage2, seg2, h->bcursor, h->ovf_key, h->ovf_cnt, h->d_ctr + 5,
                                               h->d_work);
         // pass 2: bucket by bucket in shared memory
@@ -1485,6 +1530,10 @@ int make_proj_params(double scale, ProjParams* pp, bool* wide) {
     pp->d0 = 1075 - pp->s_exp;
     pp->top = 52 + bits;
     pp->scale = scale;
+    pp->half_lo = bits >= 2 ? 1ull << (bits - 2) : 0ull;  // P of top bits: rounding at bit bits-1
+    pp->half_hi = 1ull << (bits - 1);                    // P of top+1 bits: rounding at bit bits
+    pp->thr = bits <= 10 ? 1ull << pp->top : 0ull;
+    pp->dmax = pp->top + 1021;
     *wide = bits > 10;
     return RASTER_OK;
 }
