@@ -525,7 +525,7 @@ def run_gpu(args):
             "phases_ms": {k: statistics.mean(v) for k, v in phase.items()},
             "stats": {"n_distinct": res.n_distinct, "n_significant": res.n_significant,
                       "n_clusters": res.n_clusters, "kept_tiles": int(res.key.numel()),
-                      "table_slots": r.capacity},
+                      "table_slots": r.capacity, "table": r.table_stats()},
             "roofline": roofline, "roofline_phases": roofline_phases, "gpu_launches": int(launches),
             "clocks": clocks}
 

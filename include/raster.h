@@ -162,6 +162,18 @@ int raster_point_labels(raster_handle *h, const double *xy, int64_t n, int64_t *
 int raster_point_labels_host(raster_handle *h, const double *xy_host, int64_t n, int64_t *labels_host,
                              void *stream);
 
+typedef struct {
+    int64_t capacity, occupied, probe_sum, probe_max;
+} raster_table_stats_t;
+
+/* Diagnostics of the tile table (no counterpart in the paper).  capacity:
+ * slots; occupied: tiles in the table (D); probe_sum / probe_max: over the
+ * occupied slots, the number of slots a lookup of that tile reads (1 + its
+ * distance from its home slot within the 4096-slot bucket).  probe_sum /
+ * occupied is the mean probe length of a successful lookup.  Synchronises
+ * the handle's stream. */
+int raster_table_stats(raster_handle *h, raster_table_stats_t *out);
+
 /* The whole method on HOST points in one call (Alg. 1 and the RASTER* labels,
  * Sect. 4.1): contraction of the n points at HOST xy_host (layout as for
  * raster_contract, added to whatever the handle holds), agglomeration into

@@ -254,6 +254,14 @@ class Raster:
                                           idx.numel(), ctypes.byref(m), _stream_ptr(stream)), "raster_point_groups")
         return row_start[:n_tiles + 1], idx[:m.value]
 
+    def table_stats(self) -> dict:
+        """Occupancy and probe lengths of the tile table (diagnostics)."""
+        t = _native.TableStats()
+        check(self._L.raster_table_stats(self._h, ctypes.byref(t)), "raster_table_stats")
+        occ = t.occupied
+        return {"capacity": t.capacity, "occupied": occ, "load": occ / t.capacity if t.capacity else 0.0,
+                "mean_probe": t.probe_sum / occ if occ else 0.0, "max_probe": t.probe_max}
+
     def export_tiles(self):
         """All tiles with at least one point: (key int64, count int64) CUDA tensors."""
         n = ctypes.c_int64()

@@ -39,6 +39,12 @@ class Params(ctypes.Structure):
                 ("dims", ctypes.c_uint32)]
 
 
+class TableStats(ctypes.Structure):
+    """raster_table_stats_t"""
+    _fields_ = [("capacity", ctypes.c_int64), ("occupied", ctypes.c_int64), ("probe_sum", ctypes.c_int64),
+                ("probe_max", ctypes.c_int64)]
+
+
 class Instance(ctypes.Structure):
     _fields_ = [("xy", ctypes.c_void_p), ("n", ctypes.c_int64), ("precision", ctypes.c_double),
                 ("tau", ctypes.c_uint32), ("mu", ctypes.c_uint32)]
@@ -89,6 +95,7 @@ def _declare(L):
         "raster_point_labels": (ci, [vp, vp, i64, vp, vp]),
         "raster_point_labels_host": (ci, [vp, vp, i64, vp, vp]),
         "raster_cluster_host": (ci, [vp, vp, i64, vp, ctypes.POINTER(Clusters), vp]),
+        "raster_table_stats": (ci, [vp, ctypes.POINTER(TableStats)]),
         "raster_export_tiles": (ci, [vp, vp, vp, i64, ctypes.POINTER(i64)]),
         "raster_point_groups": (ci, [vp, vp, i64, vp, vp, i64, ctypes.POINTER(i64), vp]),
         "raster_reset": (ci, [vp, vp]),

@@ -39,14 +39,4 @@ __device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned
     return r;
 }
 
-__device__ __forceinline__ void flush_counts(unsigned int newk, unsigned int st, unsigned long long* d_newkeys,
-                                             unsigned int* d_status) {
-    newk = __reduce_add_sync(0xFFFFFFFFu, newk);
-    st = __reduce_or_sync(0xFFFFFFFFu, st);
-    if ((threadIdx.x & 31) == 0) {
-        if (newk) atomicAdd(d_newkeys, (unsigned long long)newk);
-        if (st) atomicOr(d_status, st);
-    }
-}
-
 }  // namespace raster

@@ -129,32 +129,6 @@ __device__ __forceinline__ int table_add(Slot* tab, unsigned int mask, unsigned 
     return -1;
 }
 
-// Insert continuing from a first probe whose key was already loaded (k at
-// slot i).  Used when a warp issues the first probes of several points at
-// once so that their DRAM latencies overlap.
-__device__ __forceinline__ int table_add_from(Slot* tab, unsigned int mask, unsigned long long key, unsigned int c,
-                                              unsigned int i, unsigned long long k, unsigned int max_probe) {
-    for (unsigned int p = 0; p < max_probe; ++p) {
-        if (k == key) {
-            atomicAdd(&tab[i].count, c);
-            return 0;
-        }
-        if (k == kEmptyKey) {
-            k = atomicCAS(&tab[i].key, kEmptyKey, key);
-            if (k == kEmptyKey) {
-                atomicAdd(&tab[i].count, c);
-                return 1;
-            }
-            if (k == key) {
-                atomicAdd(&tab[i].count, c);
-                return 0;
-            }
-        }
-        i = (i + 1u) & mask;
-        k = __ldcg(&tab[i].key);
-    }
-    return -1;
-}
 
 // Whole-slot load through L2 (16 bytes: key, count, aux).
 __device__ __forceinline__ Slot load_slot(const Slot* s) {

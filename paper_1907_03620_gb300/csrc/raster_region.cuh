@@ -91,22 +91,6 @@ __device__ __forceinline__ int rt_add(const RegionTable& t, unsigned long long k
     return -1;
 }
 
-// Add c points to `key` only if it is already in the table (no new slot):
-// 0 if added, -1 if absent or not found within max_probe slots.
-__device__ __forceinline__ int rt_add_existing(const RegionTable& t, unsigned long long key, unsigned int c) {
-    unsigned long long i = home_slot(key, t);
-    for (unsigned int p = 0; p < t.max_probe; ++p) {
-        const unsigned long long k = load_key(&t.tab[i]);
-        if (k == key) {
-            atomicAdd(&t.tab[i].count, c);
-            return 0;
-        }
-        if (k == kEmptyKey) return -1;
-        i = next_slot(i, t);
-    }
-    return -1;
-}
-
 // The slot holding `key` (whole 16 bytes), or one with key kEmptyKey if absent.
 __device__ __forceinline__ Slot rt_lookup(const RegionTable& t, unsigned long long key, unsigned long long i, Slot sl) {
     for (unsigned int p = 0; p < t.max_probe; ++p) {

@@ -628,6 +628,31 @@ __global__ void __launch_bounds__(kBlock) k_select(Slot* tab, unsigned long long
     }
 }
 
+// Probe lengths of the occupied slots: a lookup of a tile reads 1 + its
+// distance from its home slot, along the bucket.
+__global__ void __launch_bounds__(kBlock) k_probe_stats(const Slot* __restrict__ tab, RegionTable t,
+                                                       unsigned long long* out) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long occ = 0, sum = 0;
+    unsigned int mx = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < t.cap; i += stride) {
+        const unsigned long long key = tab[i].key;
+        if (key == kEmptyKey) continue;
+        const unsigned int p = (unsigned int)((i - home_slot(key, t)) & (kBucketSlots - 1u)) + 1u;
+        ++occ;
+        sum += p;
+        mx = max(mx, p);
+    }
+    occ = __reduce_add_sync(0xFFFFFFFFu, (unsigned int)occ);
+    sum = __reduce_add_sync(0xFFFFFFFFu, (unsigned int)sum);
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((threadIdx.x & 31) == 0 && occ) {
+        atomicAdd(&out[0], occ);
+        atomicAdd(&out[1], sum);
+        atomicMax(&out[2], (unsigned long long)mx);
+    }
+}
+
 // The selection never writes more rows than its buffers hold; if it counted
 // more (the tile count was wrong), clamp the count for the kernels after it
 // and report an internal error.
@@ -1992,6 +2017,27 @@ int raster_cluster_host(raster_handle* h, const double* xy_host, int64_t n, int6
     RCHECK(h, cudaStreamSynchronize(h->copy_stream));
     RCHECK(h, cudaStreamSynchronize(h->stream));
     return rc;
+}
+
+int raster_table_stats(raster_handle* h, raster_table_stats_t* out) {
+    if (!h || !out) return RASTER_E_ARG;
+    if (hard_error(h->status)) return h->status;
+    int rc = ensure_clean(h);
+    if (rc) return rc;
+    unsigned long long* d = h->d_work + 5;  // three counters, free outside the kernels that use them
+    RCHECK(h, cudaMemsetAsync(d, 0, 3 * sizeof(unsigned long long), h->stream));
+    static int grid = grid_for((const void*)k_probe_stats, kBlock);
+    k_probe_stats<<<grid, kBlock, 0, h->stream>>>(h->tab, table_of(h), d);
+    note_launch();
+    RCHECK(h, cudaGetLastError());
+    unsigned long long v[3];
+    RCHECK(h, cudaMemcpyAsync(v, d, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    RCHECK(h, cudaStreamSynchronize(h->stream));
+    out->capacity = (int64_t)h->cap;
+    out->occupied = (int64_t)v[0];
+    out->probe_sum = (int64_t)v[1];
+    out->probe_max = (int64_t)v[2];
+    return RASTER_OK;
 }
 
 int raster_reset(raster_handle* h, void* stream) {

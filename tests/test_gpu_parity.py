@@ -264,3 +264,20 @@ def test_workload_50m_bit_exact():
     ref, ref_lab, _ = oracle.raster(xy, w.precision, w.tau, w.mu, with_labels=True)
     r, res, lab = gpu_run(xy, w.precision, w.tau, w.mu, chunks=3)
     assert_same(res, lab, ref, ref_lab)
+
+
+def test_table_stats():
+    """Diagnostics agree with the result: occupied slots = distinct tiles, and
+    probe lengths lie within a bucket."""
+    w = gen.C1_1M
+    d = torch.from_numpy(gen.points(w)).cuda()
+    r = R.Raster(w.precision, w.tau, w.mu)
+    r.contract(d)
+    res = r.agglomerate()
+    st = r.table_stats()
+    assert st["capacity"] == r.capacity and st["occupied"] == res.n_distinct
+    assert 1.0 <= st["mean_probe"] <= st["max_probe"] <= 4096
+    assert 0.0 < st["load"] <= 0.8
+    r.reset()  # a void table reads as empty
+    assert r.table_stats()["occupied"] == 0
+    r.close()
