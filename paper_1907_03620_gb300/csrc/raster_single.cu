@@ -1,25 +1,23 @@
 // Single-instance RASTER on one GB300: the contraction, agglomeration and
 // labelling kernels, and the C ABI declared in include/raster.h.
 //
-// Pipeline (Alg. 1):
-//   k_contract  -- 16-byte coalesced loads of (x, y), exact integer
-//                  projection, warp pre-aggregation of equal tiles with
-//                  __match_any_sync, insertion into the resident tile table
-//                  (Alg. 1 first loop; chunked, Sect. 3.6).
-//   k_select    -- block-scan compaction of tiles with count >= tau
-//                  (Alg. 1 second loop); records each significant tile's
-//                  index in its slot.
-//   k_hook      -- each significant tile probes its 4 forward neighbours
-//                  (adjacency at Chebyshev distance 1 is symmetric, so every
-//                  one of the 8 neighbour pairs is seen once) and unites
-//                  components (Alg. 1 while loop, as union-find).
-//   k_flatten   -- every tile points at its root.
-//   k_stats     -- component size and smallest (ix, iy) per root.
-//   k_emit      -- keep components of >= mu tiles (Alg. 1 mu test), write
-//                  (key, count, cluster id) rows and each kept tile's label
-//                  code.
-//   k_labels    -- second projection pass giving per-point labels (RASTER*,
-//                  Sect. 4.1).
+// Pipeline (Alg. 1), one handle, one device-resident tile table:
+//   contraction   k_part (exact integer projection of 16-byte loads, sort by
+//                 table region), k_bucket (sort each region's keys by
+//                 4096-slot bucket), k_insert_bucket (insert a bucket's keys
+//                 into its copy in shared memory, write it back); small
+//                 rounds into a live table use k_insert (global atomics).
+//                 Alg. 1 first loop; chunked processing, Sect. 3.6.
+//   agglomeration k_select (tiles with count >= tau, rows in their slots),
+//                 k_hook (union-find over the forward half of
+//                 neighbors(u, delta)), k_flatten, k_stats (size and smallest
+//                 tile per component), k_emit (components of >= mu tiles:
+//                 result rows and label codes).  Alg. 1 second loop, while
+//                 loop, mu test.
+//   per point     k_labels (RASTER*, Sect. 4.1) and the RASTER' groups
+//                 (Sect. 3.4).
+// The kernels live in raster_single_contract.cuh, raster_single_agglomerate.cuh
+// and raster_single_labels.cuh; this file holds the host side.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -41,7 +39,6 @@ using namespace raster;
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kContractUnroll = 4;
 // Table load: lookups (neighbour probes, labels) touch fewer sectors in a
 // sparse table, which outweighs the larger clear and scan; measured best
 // around 0.25-0.35 on the 500M-point workload.
@@ -50,965 +47,11 @@ constexpr double kGrowLoad = 0.3;     // target load after growing
 constexpr int kUnionLimit = 1 << 30;
 
 // ---------------------------------------------------------------------------
-// Block helpers
-
-// ---------------------------------------------------------------------------
 // Kernels
 
-__global__ void k_fill_table(Slot* tab, unsigned long long cap) {
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    ulonglong2 v;
-    v.x = kEmptyKey;
-    v.y = (unsigned long long)kAuxNone << 32;  // count 0, aux none
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += stride)
-        reinterpret_cast<ulonglong2*>(tab)[i] = v;
-}
-
-// Pass 1 of contraction: project a tile of kPartTile points (keys stay in
-// registers), counting-sort the keys by table region in shared memory (with
-// each key's region beside it, as a 16-bit index), reserve space in each region's
-// staging segment with one atomic per (tile, region), and append the keys in
-// coalesced runs.  Keys beyond a segment's capacity (a region far above its
-// share) go to the overflow list.
-constexpr int kPartTile = 2048;
-constexpr int kPartPer = kPartTile / kBlock;
-constexpr long long kInsertItem = 2048;
-
-template <int BLOCK = kBlock>
-__device__ __forceinline__ unsigned int block_excl_scan_bins(unsigned int* bins, int nbins, unsigned int* start,
-                                                             unsigned int* scratch) {
-    // each thread owns a contiguous run of bins
-    const int per = (nbins + BLOCK - 1) / BLOCK;
-    const int b0 = threadIdx.x * per;
-    unsigned int sum = 0;
-    for (int b = b0; b < min(b0 + per, nbins); ++b) sum += bins[b];
-    unsigned int total;
-    unsigned int off = block_excl_scan<BLOCK>(sum, scratch, &total);
-    for (int b = b0; b < min(b0 + per, nbins); ++b) {
-        start[b] = off;
-        off += bins[b];
-    }
-    __syncthreads();
-    return total;
-}
-
-// Append (key, c) to the overflow list (warp-aggregated); the list has room
-// for every key of a round, so it cannot overflow itself.
-__device__ __forceinline__ void overflow_append(bool want, unsigned long long key, unsigned int c,
-                                                unsigned long long* ovf_key, unsigned int* ovf_cnt,
-                                                unsigned long long* ovf_n) {
-    const unsigned int m = __ballot_sync(__activemask(), want);
-    if (!want) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(ovf_n, (unsigned long long)__popc(m));
-    base = __shfl_sync(m, base, leader);
-    const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
-    ovf_key[pos] = key;
-    ovf_cnt[pos] = c;
-}
-
-// Point i of an array of DIMS coordinates per point (two: one 16-byte load),
-// and its tile key, or kInvalidKey.
-template <int DIMS>
-struct PointIn {
-    double c[DIMS];
-};
-template <int DIMS>
-__device__ __forceinline__ PointIn<DIMS> load_point(const double* __restrict__ xy, long long i) {
-    PointIn<DIMS> p;
-    if (DIMS == 2) {
-        const double2 v = __ldcs(reinterpret_cast<const double2*>(xy) + i);
-        p.c[0] = v.x;
-        p.c[1] = v.y;
-    } else {
-#pragma unroll
-        for (int a = 0; a < DIMS; ++a) p.c[a] = __ldcs(xy + DIMS * i + a);
-    }
-    return p;
-}
-template <bool WIDE, int DIMS>
-__device__ __forceinline__ unsigned long long project_in(const PointIn<DIMS>& p, const ProjParams& pp) {
-    if (DIMS == 2) return project_point<WIDE>(p.c[0], p.c[1], pp);
-    return project_point3<WIDE>(p.c[0], p.c[1], p.c[DIMS - 1], pp);
-}
-
-template <bool WIDE, int DIMS>
-__global__ void __launch_bounds__(kBlock, 4) k_part(const double* __restrict__ xy, long long n, ProjParams pp,
-                                                RegionTable t, unsigned long long* __restrict__ stage,
-                                                unsigned long long seg_cap, unsigned int* __restrict__ cursor,
-                                                unsigned long long* ovf_key, unsigned int* ovf_cnt,
-                                                unsigned long long* ovf_n, unsigned int* d_status) {
-    extern __shared__ unsigned char smem[];
-    unsigned long long* s_sorted = reinterpret_cast<unsigned long long*>(smem);         // kPartTile keys
-    unsigned int* s_fill = reinterpret_cast<unsigned int*>(s_sorted + kPartTile);       // regions
-    unsigned int* s_start = s_fill + t.regions;                                         // regions
-    unsigned int* s_gbase = s_start + t.regions;                                        // regions
-    unsigned short* s_reg = reinterpret_cast<unsigned short*>(s_gbase + t.regions);     // kPartTile regions
-    __shared__ unsigned int scratch[33];
-    const int R = (int)t.regions;
-    unsigned int st = 0;
-    for (long long t0 = (long long)blockIdx.x * kPartTile; t0 < n; t0 += (long long)gridDim.x * kPartTile) {
-        for (int r = threadIdx.x; r < R; r += kBlock) s_fill[r] = 0u;
-        __syncthreads();
-        // two coordinates: all of the thread's loads in flight before projecting;
-        // three: loaded where projected (registers)
-        PointIn<DIMS> p[DIMS == 2 ? kPartPer : 1];
-        if (DIMS == 2) {
-#pragma unroll
-            for (int k = 0; k < kPartPer; ++k) {
-                const long long idx = t0 + k * kBlock + threadIdx.x;
-                if (idx < n) p[DIMS == 2 ? k : 0] = load_point<DIMS>(xy, idx);
-            }
-        }
-        unsigned long long key[kPartPer];
-        unsigned int meta[kPartPer];
-#pragma unroll
-        for (int k = 0; k < kPartPer; ++k) {
-            const long long idx = t0 + k * kBlock + threadIdx.x;
-            meta[k] = 0xFFFFFFFFu;
-            key[k] = 0ull;
-            if (idx < n) {
-                key[k] = project_in<WIDE, DIMS>(DIMS == 2 ? p[DIMS == 2 ? k : 0] : load_point<DIMS>(xy, idx), pp);
-                if (key[k] == kInvalidKey) {
-                    st |= kStRange;
-                } else {
-                    const unsigned int r = region_of(key[k], t);
-                    meta[k] = (r << 12) | atomicAdd(&s_fill[r], 1u);
-                }
-            }
-        }
-        __syncthreads();
-        const unsigned int total = block_excl_scan_bins(s_fill, R, s_start, scratch);
-        for (int r = threadIdx.x; r < R; r += kBlock)
-            if (s_fill[r]) s_gbase[r] = atomicAdd(&cursor[r], s_fill[r]);
-#pragma unroll
-        for (int k = 0; k < kPartPer; ++k) {
-            if (meta[k] != 0xFFFFFFFFu) {
-                const unsigned int r = meta[k] >> 12;
-                const unsigned int pos = s_start[r] + (meta[k] & 0xFFFu);
-                s_sorted[pos] = key[k];
-                s_reg[pos] = (unsigned short)r;
-            }
-        }
-        __syncthreads();
-        for (unsigned int j0 = 0; j0 < total; j0 += kBlock) {  // block-uniform loop (warp ballots inside)
-            const unsigned int j = j0 + threadIdx.x;
-            unsigned long long key = 0;
-            bool spill = false;
-            if (j < total) {
-                key = s_sorted[j];
-                const unsigned int r = s_reg[j];
-                const unsigned long long pos = (unsigned long long)s_gbase[r] + (j - s_start[r]);
-                if (pos < seg_cap)
-                    stage[(unsigned long long)r * seg_cap + pos] = key;
-                else
-                    spill = true;  // region far above its share: to the overflow list
-            }
-            overflow_append(spill, key, 1u, ovf_key, ovf_cnt, ovf_n);
-        }
-        __syncthreads();
-    }
-    if (st) atomicOr(d_status, st);
-}
-
-// Work items of pass 2: kInsertItem staged keys of one region; items are
-// numbered region after region.
-__global__ void __launch_bounds__(kBlock) k_region_items(const unsigned int* __restrict__ cursor, int regions,
-                                                        unsigned long long seg_cap, long long* item_start) {
-    __shared__ unsigned int scratch[33];
-    long long carry = 0;
-    for (int r0 = 0; r0 < regions; r0 += kBlock) {
-        const int r = r0 + threadIdx.x;
-        unsigned int items = 0;
-        if (r < regions) {
-            const unsigned long long c = min((unsigned long long)cursor[r], seg_cap);
-            items = (unsigned int)((c + kInsertItem - 1) / kInsertItem);
-        }
-        unsigned int tot;
-        const unsigned int off = block_excl_scan(items, scratch, &tot);
-        if (r < regions) item_start[r] = carry + off;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) item_start[regions] = carry;
-}
-
-__device__ __forceinline__ int find_region(const long long* __restrict__ start, int count, long long c) {
-    int lo = 0, hi = count;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (start[mid] <= c)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
-// Pass 1b of contraction: counting-sort each region's staged keys by bucket
-// (the 2^kBucketBits-slot unit of pass 2) into per-bucket segments of a second
-// staging buffer.  Work items are kInsertItem keys of one region; keys beyond
-// a bucket segment's capacity go to the overflow list.  A block claims its
-// next item and starts copying that item's keys to shared memory (cp.async)
-// before sorting the current one, so the claim, the region lookup and the
-// loads of one item overlap the work on the previous.
-constexpr size_t kBucketSmem = (size_t)kInsertItem * (2 * 8 + 2);  // two key buffers + bucket per key
-__global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsigned long long* __restrict__ stage,
-                                                  unsigned long long seg_cap, const unsigned int* __restrict__ cursor,
-                                                  const long long* __restrict__ item_start, int regions,
-                                                  unsigned long long* __restrict__ stage2, unsigned long long seg2,
-                                                  unsigned int* __restrict__ bcursor, unsigned long long* ovf_key,
-                                                  unsigned int* ovf_cnt, unsigned long long* ovf_n,
-                                                  unsigned long long* work) {
-    extern __shared__ __align__(16) unsigned char smem_b[];
-    unsigned long long* s_in = reinterpret_cast<unsigned long long*>(smem_b);        // 2 x kInsertItem keys
-    unsigned short* s_b = reinterpret_cast<unsigned short*>(s_in + 2 * kInsertItem); // kInsertItem
-    __shared__ unsigned int s_fill[kBlock], s_start[kBlock], s_gbase[kBlock];
-    __shared__ unsigned int scratch[33];
-    __shared__ long long s_it[2];
-    __shared__ int s_r[2];
-    __shared__ unsigned long long s_k0[2], s_k1[2];
-    const int bb = (int)t.region_bits - kBucketBits;  // buckets per region: 2^bb <= kBlock
-    const int NB = 1 << bb;
-    const unsigned int local_mask = (1u << t.region_bits) - 1u;
-    const long long total = item_start[regions];
-    // claim an item for buffer q and start copying its keys there (one group)
-    auto claim = [&](int q) {
-        if (threadIdx.x == 0) {
-            const long long it = (long long)atomicAdd(work, 1ull);
-            s_it[q] = it;
-            if (it < total) {
-                const int r = find_region(item_start, regions, it);
-                const unsigned long long cnt = min((unsigned long long)cursor[r], seg_cap);
-                const unsigned long long k0 = (unsigned long long)(it - item_start[r]) * kInsertItem;
-                s_r[q] = r;
-                s_k0[q] = k0;
-                s_k1[q] = min(k0 + kInsertItem, cnt);
-            }
-        }
-        __syncthreads();
-        if (s_it[q] < total) {
-            const unsigned long long k0 = s_k0[q], k1 = s_k1[q];
-            const unsigned long long* seg = stage + (unsigned long long)s_r[q] * seg_cap;
-#pragma unroll
-            for (int k = 0; k < (int)(kInsertItem / kBlock); ++k) {
-                const unsigned long long j = k0 + (unsigned long long)(k * kBlock + threadIdx.x);
-                if (j < k1) {
-                    const unsigned int dst = (unsigned int)__cvta_generic_to_shared(
-                        s_in + (size_t)q * kInsertItem + k * kBlock + threadIdx.x);
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(seg + j) : "memory");
-                }
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    int q = 0;
-    claim(0);
-    for (;;) {
-        claim(q ^ 1);  // the next item's keys copy while this one is sorted
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        if (threadIdx.x < NB) s_fill[threadIdx.x] = 0u;
-        __syncthreads();
-        const long long it = s_it[q];
-        if (it >= total) break;
-        const int r = s_r[q];
-        const unsigned long long k0 = s_k0[q], k1 = s_k1[q];
-        unsigned long long* s_cur = s_in + (size_t)q * kInsertItem;  // this item's keys, then its sorted keys
-        unsigned long long key[kInsertItem / kBlock];
-        unsigned int meta[kInsertItem / kBlock];
-#pragma unroll
-        for (int k = 0; k < (int)(kInsertItem / kBlock); ++k) {
-            const unsigned long long j = k0 + (unsigned long long)(k * kBlock + threadIdx.x);
-            meta[k] = 0xFFFFFFFFu;
-            key[k] = 0ull;
-            if (j < k1) {
-                key[k] = s_cur[k * kBlock + threadIdx.x];
-                const unsigned int b = (tile_hash(key[k]) & local_mask) >> kBucketBits;
-                meta[k] = (b << 12) | atomicAdd(&s_fill[b], 1u);
-            }
-        }
-        __syncthreads();  // also: every key of s_cur is in registers
-        const unsigned int n_items = block_excl_scan_bins(s_fill, NB, s_start, scratch);
-        const unsigned long long g0 = (unsigned long long)r << bb;  // first bucket of region r
-        if (threadIdx.x < NB && s_fill[threadIdx.x])
-            s_gbase[threadIdx.x] = atomicAdd(&bcursor[g0 + threadIdx.x], s_fill[threadIdx.x]);
-#pragma unroll
-        for (int k = 0; k < (int)(kInsertItem / kBlock); ++k) {
-            if (meta[k] != 0xFFFFFFFFu) {
-                const unsigned int b = meta[k] >> 12;
-                const unsigned int pos = s_start[b] + (meta[k] & 0xFFFu);
-                s_cur[pos] = key[k];
-                s_b[pos] = (unsigned short)b;
-            }
-        }
-        __syncthreads();
-        for (unsigned int j0 = 0; j0 < n_items; j0 += kBlock) {  // block-uniform loop (warp ballots inside)
-            const unsigned int j = j0 + threadIdx.x;
-            unsigned long long k = 0;
-            bool spill = false;
-            if (j < n_items) {
-                k = s_cur[j];
-                const unsigned int b = s_b[j];
-                const unsigned long long pos = (unsigned long long)s_gbase[b] + (j - s_start[b]);
-                if (pos < seg2)
-                    stage2[(g0 + b) * seg2 + pos] = k;
-                else
-                    spill = true;  // bucket far above its share: to the overflow list
-            }
-            overflow_append(spill, k, 1u, ovf_key, ovf_cnt, ovf_n);
-        }
-        __syncthreads();
-        q ^= 1;
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-// Add one point to `key` in a bucket held in shared memory (linear probing
-// from the tile's slot within the bucket, as in the global table).  Returns
-// false when the key finds neither itself nor an empty slot within
-// kBucketProbe slots (the bucket is nearly full).
-constexpr unsigned int kBucketProbe = 128;
-__device__ __forceinline__ bool bucket_add(Slot* s_tab, unsigned long long key) {
-    unsigned int i = tile_hash(key) & (kBucketSlots - 1u);
-    for (unsigned int p = 0; p < kBucketProbe; ++p) {
-        unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s_tab[i].key);
-        if (k == kEmptyKey) k = atomicCAS(&s_tab[i].key, kEmptyKey, key);
-        if (k == kEmptyKey || k == key) {
-            atomicAdd(&s_tab[i].count, 1u);
-            return true;
-        }
-        i = (i + 1u) & (kBucketSlots - 1u);
-    }
-    return false;
-}
-
-// Pass 2 of contraction: one bucket at a time per block.  The bucket's slots
-// are copied to shared memory (or cleared, for the first round after a reset,
-// when the table's contents are void), its staged keys are inserted there with
-// shared-memory atomics, and the bucket is written back whole.  New tiles are
-// counted once per bucket, as the growth of its occupied slots.  A key that
-// finds no room within kBucketProbe slots goes to the overflow list and
-// switches the bucket to passing its remaining keys there unprobed; such keys,
-// and a bucket left holding more than `limit` tiles, are counted in *d_full so
-// that the host grows the table.
-constexpr int kInsBlock = 512;
-constexpr int kInsertUnroll = 4;
-__global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ tab, unsigned long long n_buckets,
-                                                            const unsigned long long* __restrict__ stage2,
-                                                            unsigned long long seg2,
-                                                            const unsigned int* __restrict__ bcursor, int fresh,
-                                                            unsigned int limit, unsigned long long* d_newkeys,
-                                                            unsigned long long* d_full, unsigned long long* ovf_key,
-                                                            unsigned int* ovf_cnt, unsigned long long* ovf_n,
-                                                            unsigned long long* work) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    Slot* s_tab = reinterpret_cast<Slot*>(smem);  // kBucketSlots slots
-    __shared__ unsigned int s_occ0, s_occ1, s_nfull;
-    __shared__ int s_full;
-    __shared__ unsigned long long s_b;
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_b = atomicAdd(work, 1ull);
-            s_occ0 = 0u;
-            s_occ1 = 0u;
-            s_nfull = 0u;
-            s_full = 0;
-        }
-        __syncthreads();
-        const unsigned long long b = s_b;
-        if (b >= n_buckets) break;
-        const unsigned long long n = min((unsigned long long)bcursor[b], seg2);
-        if (n == 0 && !fresh) {  // untouched bucket of a live table: nothing to do
-            __syncthreads();
-            continue;
-        }
-        ulonglong2* g = reinterpret_cast<ulonglong2*>(tab + (b << kBucketBits));
-        ulonglong2* sv = reinterpret_cast<ulonglong2*>(s_tab);
-        if (fresh) {
-            ulonglong2 e;
-            e.x = kEmptyKey;
-            e.y = (unsigned long long)kAuxNone << 32;  // count 0, aux none
-            for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) sv[i] = e;
-        } else {
-            // all 4096 16-byte slot copies in flight at once, straight to shared memory
-            for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) {
-                const unsigned int dst = (unsigned int)__cvta_generic_to_shared(sv + i);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g + i) : "memory");
-            }
-            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-        }
-        __syncthreads();
-        unsigned int occ = 0;
-        if (!fresh)
-            for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) occ += sv[i].x != kEmptyKey;
-        occ = __reduce_add_sync(0xFFFFFFFFu, occ);
-        if (lane == 0 && occ) atomicAdd(&s_occ0, occ);
-        __syncthreads();  // every slot counted before any insertion
-        const unsigned long long* keys = stage2 + b * seg2;
-        unsigned int full = 0;
-        for (unsigned long long j0 = 0; j0 < n; j0 += (unsigned long long)kInsBlock * kInsertUnroll) {
-            unsigned long long kk[kInsertUnroll];
-#pragma unroll
-            for (int u = 0; u < kInsertUnroll; ++u) {
-                const unsigned long long j = j0 + (unsigned long long)(u * kInsBlock + threadIdx.x);
-                kk[u] = j < n ? __ldcs(keys + j) : kInvalidKey;
-            }
-#pragma unroll
-            for (int u = 0; u < kInsertUnroll; ++u) {
-                bool spill = false;
-                if (kk[u] != kInvalidKey) {
-                    if (*reinterpret_cast<volatile int*>(&s_full) || !bucket_add(s_tab, kk[u])) {
-                        spill = true;
-                        s_full = 1;
-                        ++full;
-                    }
-                }
-                overflow_append(spill, kk[u], 1u, ovf_key, ovf_cnt, ovf_n);
-            }
-        }
-        full = __reduce_add_sync(0xFFFFFFFFu, full);
-        if (lane == 0 && full) atomicAdd(&s_nfull, full);
-        __syncthreads();
-        occ = 0;
-        for (unsigned int i = threadIdx.x; i < kBucketSlots; i += kInsBlock) {
-            const ulonglong2 v = sv[i];
-            occ += v.x != kEmptyKey;
-            g[i] = v;
-        }
-        occ = __reduce_add_sync(0xFFFFFFFFu, occ);
-        if (lane == 0 && occ) atomicAdd(&s_occ1, occ);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (s_occ1 > s_occ0) atomicAdd(d_newkeys, (unsigned long long)(s_occ1 - s_occ0));
-            const unsigned int over = s_nfull + (s_occ1 > limit ? 1u : 0u);
-            if (over) atomicAdd(d_full, (unsigned long long)over);
-        }
-    }
-}
-
-// Pass 2 of contraction for a round much smaller than the table (a later chunk
-// of a stream): insert the staged keys straight into the table with global
-// atomics, region after region, so the table lines being updated stay in L2,
-// instead of rewriting every bucket.  Equal keys within a warp are merged.
-// New tiles are only created while the table holds fewer than `new_limit`
-// tiles; past it, and for probe sequences longer than the bound, keys go to
-// the overflow list with their counts.  Table plus list always hold the exact
-// counts; the host grows the table and re-inserts the list.
-__global__ void __launch_bounds__(kBlock) k_insert(RegionTable t, const unsigned long long* __restrict__ stage,
-                                                  unsigned long long seg_cap, const unsigned int* __restrict__ cursor,
-                                                  const long long* __restrict__ item_start, int regions,
-                                                  unsigned long long new_limit, unsigned long long* d_newkeys,
-                                                  unsigned long long* ovf_key, unsigned int* ovf_cnt,
-                                                  unsigned long long* ovf_n, unsigned long long* work) {
-    __shared__ int s_allow;
-    __shared__ unsigned int s_new;
-    __shared__ long long s_it;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long total = item_start[regions];
-    for (;;) {
-        // items are taken in order from a shared counter, so all blocks work on
-        // one narrow window of regions (a static stride lets blocks drift apart)
-        if (threadIdx.x == 0) {
-            s_it = (long long)atomicAdd(work, 1ull);
-            s_allow = *reinterpret_cast<volatile unsigned long long*>(d_newkeys) < new_limit;
-            s_new = 0u;
-        }
-        __syncthreads();
-        const long long it = s_it;
-        if (it >= total) break;
-        const bool allow = s_allow != 0;
-        const int r = find_region(item_start, regions, it);
-        const unsigned long long cnt = min((unsigned long long)cursor[r], seg_cap);
-        const unsigned long long k0 = (unsigned long long)(it - item_start[r]) * kInsertItem;
-        const unsigned long long k1 = min(k0 + kInsertItem, cnt);
-        const unsigned long long* seg = stage + (unsigned long long)r * seg_cap;
-        unsigned int newk = 0;
-        for (unsigned long long base = k0 + warp * 32; base < k0 + kInsertItem; base += kBlock) {
-            const unsigned long long k = base + lane;
-            const unsigned long long key = k < k1 ? __ldcs(seg + k) : kInvalidKey;
-            const unsigned int grp = __match_any_sync(0xFFFFFFFFu, key);
-            const unsigned int c = (unsigned int)__popc(grp);
-            bool spill = false;
-            if (lane == __ffs(grp) - 1 && key != kInvalidKey) {
-                // past the new-tile limit the table is due to grow: spill at once
-                const int rc = allow ? rt_add(t, key, c) : -1;
-                if (rc > 0)
-                    ++newk;
-                else if (rc < 0)
-                    spill = true;
-            }
-            overflow_append(spill, key, c, ovf_key, ovf_cnt, ovf_n);
-        }
-        newk = __reduce_add_sync(0xFFFFFFFFu, newk);
-        if (lane == 0 && newk) atomicAdd(&s_new, newk);
-        __syncthreads();
-        if (threadIdx.x == 0 && s_new) atomicAdd(d_newkeys, (unsigned long long)s_new);
-        __syncthreads();
-    }
-}
-
-// Re-insert the overflow list (after the table has grown); must succeed.
-__global__ void k_reinsert(RegionTable t, const unsigned long long* __restrict__ ovf_key,
-                           const unsigned int* __restrict__ ovf_cnt, unsigned long long n,
-                           unsigned long long* d_newkeys, unsigned int* d_status) {
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    unsigned int newk = 0, st = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int rc = rt_add(t, ovf_key[i], ovf_cnt[i]);
-        if (rc > 0)
-            ++newk;
-        else if (rc < 0)
-            st |= kStFull;
-    }
-    if (newk) atomicAdd(d_newkeys, (unsigned long long)newk);
-    if (st) atomicOr(d_status, st);
-}
-
-__global__ void k_rehash(const Slot* __restrict__ old_tab, unsigned long long old_cap, RegionTable t,
-                         unsigned int* d_status) {
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    unsigned int st = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < old_cap; i += stride) {
-        const Slot s = old_tab[i];
-        if (s.key != kEmptyKey && rt_add(t, s.key, s.count) < 0) st |= kStFull;
-    }
-    if (st) atomicOr(d_status, st);
-}
-
-// Compaction of occupied slots with count >= min_count into (key, count, slot)
-// rows.  With min_count = tau this is the significant-tile selection; each
-// selected slot's aux receives its row index.
-constexpr int kSelItems = 8;
-__global__ void __launch_bounds__(kBlock) k_select(Slot* tab, unsigned long long cap, unsigned int min_count,
-                                                  unsigned long long* out_key, unsigned int* out_cnt,
-                                                  unsigned int* out_slot, unsigned long long* d_rows,
-                                                  unsigned long long row_cap, int write_aux, int marked) {
-    __shared__ unsigned int scratch[33];
-    __shared__ unsigned long long s_base;
-    const unsigned long long tile = (unsigned long long)kBlock * kSelItems;
-    for (unsigned long long t0 = (unsigned long long)blockIdx.x * tile; t0 < cap;
-         t0 += (unsigned long long)gridDim.x * tile) {
-        unsigned long long k[kSelItems];
-        unsigned int c[kSelItems];
-        unsigned int flags = 0;
-#pragma unroll
-        for (int it = 0; it < kSelItems; ++it) {
-            const unsigned long long idx = t0 + (unsigned long long)it * kBlock + threadIdx.x;
-            k[it] = kEmptyKey;
-            c[it] = 0;
-            bool mark = false;
-            if (idx < cap) {
-                const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(tab) + idx);
-                k[it] = v.x;
-                c[it] = (unsigned int)v.y;
-                mark = marked && (unsigned int)(v.y >> 32) == kAuxGroup;
-            }
-            if (k[it] != kEmptyKey && (c[it] >= min_count || mark)) flags |= 1u << it;
-        }
-        unsigned int total;
-        unsigned int off = block_excl_scan((unsigned int)__popc(flags), scratch, &total);
-        if (threadIdx.x == 0) s_base = total ? atomicAdd(d_rows, (unsigned long long)total) : 0ull;
-        __syncthreads();
-        const unsigned long long base = s_base;
-#pragma unroll
-        for (int it = 0; it < kSelItems; ++it) {
-            if (flags & (1u << it)) {
-                const unsigned long long idx = t0 + (unsigned long long)it * kBlock + threadIdx.x;
-                const unsigned long long row = base + off++;
-                if (row >= row_cap) continue;  // more rows than the tile count allows: reported by the host
-                out_key[row] = k[it];
-                out_cnt[row] = c[it];
-                if (out_slot) out_slot[row] = (unsigned int)idx;
-                if (write_aux) tab[idx].aux = (unsigned int)row;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Probe lengths of the occupied slots: a lookup of a tile reads 1 + its
-// distance from its home slot, along the bucket.
-__global__ void __launch_bounds__(kBlock) k_probe_stats(const Slot* __restrict__ tab, RegionTable t,
-                                                       unsigned long long* out) {
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    unsigned long long occ = 0, sum = 0;
-    unsigned int mx = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < t.cap; i += stride) {
-        const unsigned long long key = tab[i].key;
-        if (key == kEmptyKey) continue;
-        const unsigned int p = (unsigned int)((i - home_slot(key, t)) & (kBucketSlots - 1u)) + 1u;
-        ++occ;
-        sum += p;
-        mx = max(mx, p);
-    }
-    occ = __reduce_add_sync(0xFFFFFFFFu, (unsigned int)occ);
-    sum = __reduce_add_sync(0xFFFFFFFFu, (unsigned int)sum);
-    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    if ((threadIdx.x & 31) == 0 && occ) {
-        atomicAdd(&out[0], occ);
-        atomicAdd(&out[1], sum);
-        atomicMax(&out[2], (unsigned long long)mx);
-    }
-}
-
-// The selection never writes more rows than its buffers hold; if it counted
-// more (the tile count was wrong), clamp the count for the kernels after it
-// and report an internal error.
-__global__ void k_clamp_rows(unsigned long long* d_rows, unsigned long long row_cap, unsigned int* d_status) {
-    if (*d_rows > row_cap) {
-        *d_rows = row_cap;
-        atomicOr(d_status, kStInternal);
-    }
-}
-
-__global__ void k_uf_init(const unsigned long long* d_nsig, int* parent, unsigned int* csize,
-                          unsigned long long* cmin) {
-    const long long S = (long long)*d_nsig;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += stride) {
-        parent[i] = (int)i;
-        csize[i] = 0u;
-        cmin[i] = ~0ull;
-    }
-}
-
-// Next chunk of kBlock rows for this block, taken in order from a shared
-// counter: rows in flight stay in one window (and so do the table regions and
-// union-find roots they touch).  Returns a value >= limit when done.
-__device__ __forceinline__ long long next_chunk(unsigned long long* work, long long* s_chunk) {
-    if (threadIdx.x == 0) *s_chunk = (long long)atomicAdd(work, 1ull) * kBlock;
-    __syncthreads();
-    const long long c = *s_chunk;
-    __syncthreads();
-    return c;
-}
-
-// The forward half of neighbors(u, delta) (Alg. 1): offsets (dx, dy) with
-// dx > 0, or dx = 0 and dy > 0, inside the Chebyshev or Manhattan ball of
-// radius delta (Sect. 3.2).  Adjacency is symmetric, so these visit every
-// neighbour pair once.
-constexpr int kMaxFwd = ((2 * RASTER_MAX_DELTA + 1) * (2 * RASTER_MAX_DELTA + 1) - 1) / 2;
-struct NbrSet {
-    int n;
-    int dims;
-    signed char dx[kMaxFwd];
-    signed char dy[kMaxFwd];
-    signed char dz[kMaxFwd];
-};
-
-// One thread per (significant tile, forward neighbour); a tile's lookups and
-// unions run in parallel threads.  The default neighbourhood (Chebyshev
-// distance 1: (x+1, y-1), (x+1, y), (x+1, y+1), (x, y+1)) is specialised.
-// Significance is read from the slot: the selection wrote each significant
-// tile's row into aux, every other slot holds kAuxNone.
-template <bool GENERAL>
-__global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
-                                                const unsigned long long* __restrict__ sig_key, RegionTable t,
-                                                const NbrSet* __restrict__ nbr, int nfwd, int dims, int* parent,
-                                                unsigned long long* work, unsigned int* d_status) {
-    __shared__ long long s_chunk;
-    const int F = GENERAL ? nfwd : 4;
-    const long long SF = (long long)F * (long long)*d_nsig;
-    unsigned int st = 0;
-    for (long long w0 = next_chunk(work, &s_chunk); w0 < SF; w0 = next_chunk(work, &s_chunk)) {
-        const long long w = w0 + threadIdx.x;
-        if (w >= SF) continue;
-        long long i;
-        int dx, dy, dz = 0;
-        if (GENERAL) {
-            i = w / F;
-            const int q = (int)(w - i * F);
-            dx = __ldg(&nbr->dx[q]);
-            dy = __ldg(&nbr->dy[q]);
-            dz = __ldg(&nbr->dz[q]);
-        } else {
-            i = w >> 2;
-            const int q = (int)(w & 3);
-            dx = q < 3 ? 1 : 0;
-            dy = q < 3 ? q - 1 : 1;
-        }
-        const unsigned long long key = sig_key[i];
-        unsigned long long nk;
-        if (GENERAL && dims == 3) {
-            const int nx = key3(key, 0) + dx, ny = key3(key, 1) + dy, nz = key3(key, 2) + dz;
-            if (nx < kMin3 || nx > kMax3 || ny < kMin3 || ny > kMax3 || nz < kMin3 || nz > kMax3) continue;
-            nk = pack_key3(nx, ny, nz);
-        } else {
-            const long long nx = (long long)key_x(key) + dx;
-            const long long ny = (long long)key_y(key) + dy;
-            if (nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll) continue;
-            nk = pack_key((int)nx, (int)ny);
-        }
-        const Slot nb = rt_get(t, nk);
-        if (nb.key != nk || nb.aux == kAuxNone) continue;
-        if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
-    }
-    if (st) atomicOr(d_status, st);
-}
-
-// The post-processing of Sect. 3.6 ("disadvantageous grid layouts"): an
-// occupied tile with fewer than tau points is marked (aux = kAuxGroup) when
-// one of the four 2 x 2 tile groups it belongs to holds at least tau points;
-// the selection then takes it as significant.  One thread per slot reads the
-// counts of the tile's eight neighbours; slots are taken in order, chunk by
-// chunk, so the lookups stay within the few regions in flight.
-__global__ void __launch_bounds__(kBlock) k_groups(Slot* tab, RegionTable t, unsigned int tau,
-                                                  unsigned long long* work) {
-    __shared__ long long s_chunk;
-    for (long long c0 = next_chunk(work, &s_chunk); c0 < (long long)t.cap; c0 = next_chunk(work, &s_chunk)) {
-        const unsigned long long i = (unsigned long long)c0 + threadIdx.x;
-        if (i >= t.cap) continue;
-        const Slot sl = load_slot(&tab[i]);
-        if (sl.key == kEmptyKey || sl.count >= tau) continue;
-        const long long x = key_x(sl.key), y = key_y(sl.key);
-        unsigned long long c[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                c[a][b] = 0ull;
-                const long long nx = x + a - 1, ny = y + b - 1;
-                if (a == 1 && b == 1) {
-                    c[a][b] = sl.count;
-                } else if (nx >= -2147483647ll && nx <= 2147483646ll && ny >= -2147483647ll && ny <= 2147483646ll) {
-                    const unsigned long long nk = pack_key((int)nx, (int)ny);
-                    const Slot nb = rt_get(t, nk);
-                    if (nb.key == nk) c[a][b] = nb.count;
-                }
-            }
-        bool keep = false;
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-                keep |= c[a][b] + c[a + 1][b] + c[a][b + 1] + c[a + 1][b + 1] >= tau;
-        if (keep) tab[i].aux = kAuxGroup;
-    }
-}
-
-__global__ void __launch_bounds__(kBlock) k_flatten(const unsigned long long* d_nsig, int* parent,
-                                                   unsigned long long* work) {
-    __shared__ long long s_chunk;
-    const long long S = (long long)*d_nsig;
-    for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
-        const long long i = c + threadIdx.x;
-        if (i < S) parent[i] = uf_root(parent, (int)i);
-    }
-}
-
-// Order of keys as unsigned integers: (x, y) order after flipping both sign
-// bits of a two-coordinate key; a three-coordinate key is in (x, y, z) order
-// as it stands.
-constexpr unsigned long long kOrderXor2 = 0x8000000080000000ull, kOrderXor3 = 0ull;
-
-// A kept tile's label code: offsets to its cluster-id tile for two
-// coordinates, the escape to its result row for three.
-__device__ __forceinline__ unsigned int label_code_d(unsigned long long key, unsigned long long cid, unsigned int row,
-                                                     int dims) {
-    return dims == 3 ? (0x80000000u | row) : label_code(key, cid, row);
-}
-
-__global__ void __launch_bounds__(kBlock) k_stats(const unsigned long long* d_nsig,
-                                                 const unsigned long long* __restrict__ sig_key,
-                                                 const int* __restrict__ parent, unsigned int* csize,
-                                                 unsigned long long* cmin, unsigned long long* work,
-                                                 unsigned long long order_xor) {
-    __shared__ long long s_chunk;
-    const long long S = (long long)*d_nsig;
-    for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
-        const long long i = c + threadIdx.x;
-        if (i < S) {
-            const int r = parent[i];
-            atomicAdd(&csize[r], 1u);
-            atomicMin(&cmin[r], sig_key[i] ^ order_xor);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kBlock) k_emit(const unsigned long long* d_nsig,
-                                                const unsigned long long* __restrict__ sig_key,
-                                                const unsigned int* __restrict__ sig_cnt,
-                                                const unsigned int* __restrict__ sig_slot,
-                                                const int* __restrict__ parent, const unsigned int* __restrict__ csize,
-                                                const unsigned long long* __restrict__ cmin, unsigned int mu,
-                                                Slot* tab, unsigned long long* out_key, unsigned int* out_cnt,
-                                                unsigned long long* out_cid, unsigned int* out_slot,
-                                                unsigned long long* d_nkept, unsigned long long* d_nclusters,
-                                                unsigned long long* work, unsigned long long order_xor, int dims) {
-    __shared__ unsigned int scratch[33];
-    __shared__ unsigned long long s_base;
-    __shared__ long long s_chunk;
-    const long long S = (long long)*d_nsig;
-    unsigned int clusters = 0;
-    for (long long t0 = next_chunk(work, &s_chunk); t0 < S; t0 = next_chunk(work, &s_chunk)) {
-        const long long i = t0 + threadIdx.x;
-        bool keep = false;
-        unsigned long long key = 0, cid = 0;
-        int r = 0;
-        if (i < S) {
-            r = parent[i];
-            keep = csize[r] >= mu;
-            key = sig_key[i];
-            cid = cmin[r] ^ order_xor;
-            if (keep && r == (int)i) ++clusters;
-        }
-        unsigned int total;
-        const unsigned int off = block_excl_scan(keep ? 1u : 0u, scratch, &total);
-        if (threadIdx.x == 0) s_base = total ? atomicAdd(d_nkept, (unsigned long long)total) : 0ull;
-        __syncthreads();
-        if (i < S) {
-            unsigned int code = kAuxNone;
-            if (keep) {
-                const unsigned long long row = s_base + off;
-                out_key[row] = key;
-                out_cnt[row] = sig_cnt[i];
-                out_cid[row] = cid;
-                out_slot[row] = sig_slot[i];
-                code = label_code_d(key, cid, (unsigned int)row, dims);
-            }
-            tab[sig_slot[i]].aux = code;
-        }
-        __syncthreads();
-    }
-    clusters = __reduce_add_sync(0xFFFFFFFFu, clusters);
-    if ((threadIdx.x & 31) == 0 && clusters) atomicAdd(d_nclusters, (unsigned long long)clusters);
-}
-
-template <bool WIDE, int DIMS>
-__global__ void k_labels(const double* __restrict__ xy, long long n, ProjParams pp, RegionTable t, unsigned int tau,
-                         const long long* __restrict__ cid_rows, long long* __restrict__ labels,
-                         unsigned int* d_status) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    unsigned int st = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned long long key = project_in<WIDE, DIMS>(load_point<DIMS>(xy, i), pp);
-        long long lab = (long long)kEmptyKey;
-        if (key == kInvalidKey) {
-            st |= kStRange;
-        } else {
-            const Slot sl = rt_get(t, key);
-            if (sl.key == key) lab = label_decode(key, sl.aux, cid_rows);  // kAuxNone decodes to noise
-        }
-        __stcs(labels + i, lab);
-    }
-    if (st) atomicOr(d_status, st);
-}
-
-// RASTER' (Sect. 3.4): the points of every kept tile, as a CSR over result
-// rows.  The slots of kept tiles temporarily hold their result row in aux.
-__global__ void k_aux_rows(const unsigned long long* d_nkept, const unsigned int* __restrict__ out_slot, Slot* tab) {
-    const long long K = (long long)*d_nkept;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < K; r += stride)
-        tab[out_slot[r]].aux = (unsigned int)r;
-}
-
-__global__ void k_aux_codes(const unsigned long long* d_nkept, const unsigned int* __restrict__ out_slot,
-                            const unsigned long long* __restrict__ out_key,
-                            const unsigned long long* __restrict__ out_cid, Slot* tab, int dims) {
-    const long long K = (long long)*d_nkept;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < K; r += stride)
-        tab[out_slot[r]].aux = label_code_d(out_key[r], out_cid[r], (unsigned int)r, dims);
-}
-
-template <bool WIDE, int DIMS>
-__global__ void k_group_count(const double* __restrict__ xy, long long n, ProjParams pp, RegionTable t,
-                              unsigned int tau, unsigned int* row_count, int* point_row, unsigned int* d_status) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    unsigned int st = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned long long key = project_in<WIDE, DIMS>(load_point<DIMS>(xy, i), pp);
-        int row = -1;
-        if (key == kInvalidKey) {
-            st |= kStRange;
-        } else {
-            const Slot sl = rt_get(t, key);
-            if (sl.key == key && sl.aux != kAuxNone) {
-                row = (int)sl.aux;
-                atomicAdd(&row_count[row], 1u);
-            }
-        }
-        point_row[i] = row;
-    }
-    if (st) atomicOr(d_status, st);
-}
-
-// Exclusive scan of row_count[0..K) into row_start[0..K]; three launches.
-constexpr int kScanTile = kBlock * 8;
-__global__ void __launch_bounds__(kBlock) k_scan_tiles(const unsigned long long* d_nkept,
-                                                      const unsigned int* __restrict__ in, long long* out,
-                                                      long long* tile_sums) {
-    __shared__ unsigned int scratch[33];
-    const long long K = (long long)*d_nkept;
-    for (long long t0 = (long long)blockIdx.x * kScanTile; t0 < K; t0 += (long long)gridDim.x * kScanTile) {
-        unsigned int v[8];
-        unsigned int sum = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const long long i = t0 + threadIdx.x * 8 + k;
-            v[k] = i < K ? in[i] : 0u;
-            sum += v[k];
-        }
-        unsigned int total;
-        unsigned int off = block_excl_scan(sum, scratch, &total);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const long long i = t0 + threadIdx.x * 8 + k;
-            if (i < K) out[i] = off;
-            off += v[k];
-        }
-        if (threadIdx.x == 0) tile_sums[t0 / kScanTile] = total;
-    }
-}
-
-__global__ void __launch_bounds__(kBlock) k_scan_sums(const unsigned long long* d_nkept, long long* tile_sums,
-                                                     long long* out) {
-    __shared__ long long s_part[kBlock];
-    const long long K = (long long)*d_nkept;
-    const long long T = (K + kScanTile - 1) / kScanTile;
-    // each thread owns a contiguous run of tile sums
-    const long long per = (T + kBlock - 1) / kBlock;
-    const long long a = threadIdx.x * per, b = min(a + per, T);
-    long long sum = 0;
-    for (long long j = a; j < b; ++j) sum += tile_sums[j];
-    s_part[threadIdx.x] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        for (int j = 0; j < kBlock; ++j) {
-            const long long x = s_part[j];
-            s_part[j] = acc;
-            acc += x;
-        }
-        out[K] = acc;  // total points in kept tiles
-    }
-    __syncthreads();
-    long long acc = s_part[threadIdx.x];
-    for (long long j = a; j < b; ++j) {
-        const long long x = tile_sums[j];
-        tile_sums[j] = acc;
-        acc += x;
-    }
-}
-
-__global__ void k_scan_add(const unsigned long long* d_nkept, const long long* __restrict__ tile_sums, long long* out) {
-    const long long K = (long long)*d_nkept;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride)
-        out[i] += tile_sums[i / kScanTile];
-}
-
-__global__ void k_group_scatter(long long n, const int* __restrict__ point_row, const long long* __restrict__ row_start,
-                                unsigned int* cursor, long long* point_index) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int r = point_row[i];
-        if (r >= 0) point_index[row_start[r] + atomicAdd(&cursor[r], 1u)] = i;
-    }
-}
+#include "raster_single_contract.cuh"
+#include "raster_single_agglomerate.cuh"
+#include "raster_single_labels.cuh"
 
 // ---------------------------------------------------------------------------
 // Host side
