@@ -22,6 +22,10 @@
  *   - significant: count >= tau; kept: cluster size in tiles >= mu;
  *   - cluster id = key of the cluster's smallest tile in (ix, iy)
  *     lexicographic order (ix first); noise label = RASTER_NOISE.
+ * raster_create_ex extends the neighbourhood (Chebyshev or Manhattan
+ * distance delta, Sect. 3.2), adds the 2 x 2 group rule of Sect. 3.6, and
+ * takes points with three coordinates (its own key format, see
+ * raster_params); the defaults above are unchanged.
  *
  * Memory: points and labels are caller buffers; tables and results live in
  * device memory owned by the handle.  "stream" arguments are cudaStream_t
