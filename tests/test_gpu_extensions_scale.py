@@ -66,7 +66,7 @@ def test_three_coordinates_100m_sampled():
         seen, stack = {int(cid)}, [int(cid)]
         while stack:
             u = stack.pop()
-            x, y, z = (int(v) for v in oracle.unpack3(np.array([u])))
+            x, y, z = (int(v[0]) for v in oracle.unpack3(np.array([u])))
             nb = oracle.pack3(x + offs[:, 0], y + offs[:, 1], z + offs[:, 2])
             for k, c in zip(nb.tolist(), count_of(nb).tolist()):
                 if c >= tau and k not in seen:
