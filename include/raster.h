@@ -227,7 +227,7 @@ int raster_reset(raster_handle *h, void *stream);
 int raster_status(raster_handle *h);
 
 /* The scale s = 10^precision used by project() (Alg. 1; Sect. 3.2), as the one
- * double both the kernels and any checker must multiply by. */
+ * double both the kernels and any other implementation must multiply by. */
 double raster_get_scale(const raster_handle *h);
 
 /* Table capacity in slots.  Diagnostics; no counterpart in the paper. */
