@@ -122,7 +122,7 @@ struct raster_handle {
     unsigned int* out_slot = nullptr;  // table slot of each result row
     raster_clusters result{};
     // RASTER' point groups: row of each point, per-row counters
-    int* point_row = nullptr;
+    unsigned long long* point_rr = nullptr;  // (row << 32 | rank within the row) per point
     long long point_row_cap = 0;
     unsigned int* row_count = nullptr;
     long long* scan_sums = nullptr;
@@ -568,7 +568,7 @@ template <bool WIDE, int DIMS>
 void launch_group_count(raster_handle* h, const double* xy, long long n) {
     static int grid = grid_for((const void*)k_group_count<WIDE, DIMS>, kBlock);
     k_group_count<WIDE, DIMS><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
-        xy, n, h->pp, table_of(h), h->tau, h->row_count, h->point_row, h->d_status);
+        xy, n, h->pp, table_of(h), h->tau, h->row_count, h->point_rr, h->d_status);
 }
 
 bool misaligned(const void* p, int dims = 2) { return ((uintptr_t)p & (dims == 3 ? 7u : 15u)) != 0; }
@@ -908,13 +908,13 @@ int raster_point_groups(raster_handle* h, const double* xy, int64_t n, int64_t* 
     h->stream = (cudaStream_t)stream;
     cudaStream_t s = h->stream;
     const long long K = h->result.n_tiles;
-    // scratch: a row per point, a counter and a cursor per result row
+    // scratch: (row, rank) per point, a counter per result row
     if (n > h->point_row_cap) {
         RCHECK(h, cudaStreamSynchronize(s));
-        if (h->point_row) cudaFree(h->point_row);
-        h->point_row = nullptr;
+        if (h->point_rr) cudaFree(h->point_rr);
+        h->point_rr = nullptr;
         h->point_row_cap = 0;
-        RCHECK(h, cudaMalloc(&h->point_row, sizeof(int) * (size_t)std::max<long long>(n, 1)));
+        RCHECK(h, cudaMalloc(&h->point_rr, sizeof(unsigned long long) * (size_t)std::max<long long>(n, 1)));
         h->point_row_cap = std::max<long long>(n, 1);
     }
     if (K + 1 > h->row_count_cap) {
@@ -954,10 +954,9 @@ int raster_point_groups(raster_handle* h, const double* xy, int64_t n, int64_t* 
     *n_grouped = m;
     if (m > capacity || (m > 0 && !point_index)) return RASTER_E_ARG;
     if (m > 0) {
-        RCHECK(h, cudaMemsetAsync(h->row_count, 0, sizeof(unsigned int) * (size_t)K, s));  // reuse as cursors
         static int g2 = grid_for((const void*)k_group_scatter, kBlock);
         k_group_scatter<<<(int)std::min<long long>(g2, (n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-            n, h->point_row, rs, h->row_count, reinterpret_cast<long long*>(point_index));
+            n, h->point_rr, rs, reinterpret_cast<long long*>(point_index));
         note_launch();
         RCHECK(h, cudaGetLastError());
     }
@@ -1121,7 +1120,7 @@ int raster_destroy(raster_handle* h) {
     void* bufs[] = {h->tab,    h->d_ctr,   h->d_status, h->sig_key, h->sig_cnt, h->sig_slot, h->parent,
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
                     h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
-                    h->ovf_cnt, h->d_work, h->out_slot, h->point_row, h->row_count, h->scan_sums,
+                    h->ovf_cnt, h->d_work, h->out_slot, h->point_rr, h->row_count, h->scan_sums,
                     h->stage2,  h->bcursor, h->d_nbr, h->res_xy};
     for (void* p : bufs)
         if (p) cudaFree(p);

@@ -43,24 +43,25 @@ __global__ void k_aux_codes(const unsigned long long* d_nkept, const unsigned in
         tab[out_slot[r]].aux = label_code_d(out_key[r], out_cid[r], (unsigned int)r, dims);
 }
 
+constexpr unsigned long long kNoRow = ~0ull;  // a point outside every kept tile
+
 template <bool WIDE, int DIMS>
 __global__ void k_group_count(const double* __restrict__ xy, long long n, ProjParams pp, RegionTable t,
-                              unsigned int tau, unsigned int* row_count, int* point_row, unsigned int* d_status) {
+                              unsigned int tau, unsigned int* row_count, unsigned long long* point_rr,
+                              unsigned int* d_status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     unsigned int st = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const unsigned long long key = project_in<WIDE, DIMS>(load_point<DIMS>(xy, i), pp);
-        int row = -1;
+        unsigned long long rr = kNoRow;  // (row << 32 | rank of the point within its row)
         if (key == kInvalidKey) {
             st |= kStRange;
         } else {
             const Slot sl = rt_get(t, key);
-            if (sl.key == key && sl.aux != kAuxNone) {
-                row = (int)sl.aux;
-                atomicAdd(&row_count[row], 1u);
-            }
+            if (sl.key == key && sl.aux != kAuxNone)
+                rr = ((unsigned long long)sl.aux << 32) | atomicAdd(&row_count[sl.aux], 1u);
         }
-        point_row[i] = row;
+        point_rr[i] = rr;
     }
     if (st) atomicOr(d_status, st);
 }
@@ -130,11 +131,13 @@ __global__ void k_scan_add(const unsigned long long* d_nkept, const long long* _
         out[i] += tile_sums[i / kScanTile];
 }
 
-__global__ void k_group_scatter(long long n, const int* __restrict__ point_row, const long long* __restrict__ row_start,
-                                unsigned int* cursor, long long* point_index) {
+// Each grouped point goes to its row's start plus the rank it drew while
+// counting, so the scatter takes no atomics.
+__global__ void k_group_scatter(long long n, const unsigned long long* __restrict__ point_rr,
+                                const long long* __restrict__ row_start, long long* point_index) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int r = point_row[i];
-        if (r >= 0) point_index[row_start[r] + atomicAdd(&cursor[r], 1u)] = i;
+        const unsigned long long rr = point_rr[i];
+        if (rr != kNoRow) point_index[row_start[rr >> 32] + (unsigned int)rr] = i;
     }
 }
