@@ -651,6 +651,17 @@ def run_gpu(args):
 
         e2e_step()
         torch.cuda.synchronize()
+        # the machine's host link, for context: 2 GB of points in, 1 GB of labels out
+        q = w.n // 4
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xy[:q].copy_(host[:q], non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = POINT_BYTES * q / (time.perf_counter() - t0) / 1e9
+        t0 = time.perf_counter()
+        lab_host[:q].copy_(labels[:q], non_blocking=True)
+        torch.cuda.synchronize()
+        d2h_gbs = 8 * q / (time.perf_counter() - t0) / 1e9
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
@@ -661,7 +672,8 @@ def run_gpu(args):
         dt = max_over_ranks((time.perf_counter() - t0) / n_e2e, dev)
         line["e2e"] = {"value": whole_job_rate(world, w.n, dt), "unit": "points/s", "h2d_bytes_per_step": POINT_BYTES * w.n,
                        "d2h_bytes_per_step": 8 * w.n, "ms_per_step": dt * 1e3, "steps": n_e2e,
-                       "call": "raster_cluster_host (points copied once; labels copied back)"}
+                       "call": "raster_cluster_host (points copied once; labels copied back)",
+                       "link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs}}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile:
         rate, dt, desc = oracle_sample(w, args.cpu_sample)
