@@ -158,7 +158,12 @@ int raster_agglomerate(raster_handle *h, raster_clusters *out);
  * each point again and writes its tile's cluster id, or RASTER_NOISE.
  * Requires a preceding raster_agglomerate with no contract since.
  * xy: DEVICE, n x 2 float64, 16-byte aligned; labels: DEVICE int64[n],
- * caller-owned.  Asynchronous on `stream`. */
+ * caller-owned.  Asynchronous on `stream`, except that the first call after
+ * an agglomeration of two-coordinate points whose tile table exceeds 64 MiB
+ * synchronises once, to size an index of the kept tiles by 8 x 8-tile block
+ * that answers most lookups from L2.  The environment variable
+ * RASTER_LABEL_INDEX, read when the handle is created, forces that index on
+ * ("1") or off ("0"); the labels are the same either way. */
 int raster_point_labels(raster_handle *h, const double *xy, int64_t n, int64_t *labels, void *stream);
 
 /* Per-point labels (RASTER*, Sect. 4.1) as raster_point_labels, with HOST xy

@@ -10,8 +10,8 @@
 //                 Alg. 1 first loop; chunked processing, Sect. 3.6.
 //   agglomeration k_select (tiles with count >= tau, rows in their slots),
 //                 k_hook (union-find over the forward half of
-//                 neighbors(u, delta)), k_flatten, k_stats (size and smallest
-//                 tile per component), k_emit (components of >= mu tiles:
+//                 neighbors(u, delta)), k_flatten_stats (root, size and
+//                 smallest tile per component), k_emit (components of >= mu tiles:
 //                 result rows and label codes).  Alg. 1 second loop, while
 //                 loop, mu test.
 //   per point     k_labels (RASTER*, Sect. 4.1) and the RASTER' groups
@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <atomic>
 #include <new>
@@ -147,6 +148,19 @@ struct raster_handle {
     bool fresh = false;
 
     unsigned long long* d_work = nullptr;  // work counters of the ordered kernels (8)
+
+    // block index of the kept tiles for the labels (two coordinates): rebuilt
+    // by the first labels call after each agglomeration
+    int lidx_mode = 0;         // 0: when the tile table outgrows L2; 1: always; -1: never
+    bool lidx_stale = true;
+    bool lidx_on = false;
+    unsigned long long* lidx = nullptr;   // 32-byte buckets of two entries
+    unsigned long long lidx_alloc = 0;    // buckets
+    unsigned long long lidx_buckets = 0;  // buckets in use: regions x share
+    unsigned long long lidx_share = 0;
+    unsigned int* lbitmap = nullptr;    // linear-counting bitmap
+    unsigned long long lbitmap_words = 0;
+    unsigned long long* d_lidx = nullptr;  // [0] zero bits of the bitmap, [1] build failure flag
 
     // host staging (contract_host / labels_host)
     cudaStream_t copy_stream = nullptr;
@@ -556,12 +570,89 @@ int ensure_stage(raster_handle* h) {
     return RASTER_OK;
 }
 
+constexpr double kLidxMinTableBytes = 64.0 * (1 << 20);  // a smaller tile table stays in L2 by itself
+
+// Build the block index of the kept tiles (raster_single_labels.cuh) for the
+// labels, once per agglomeration: estimate the number of blocks by linear
+// counting (one synchronisation), size the index for kLidxLoad, insert.  An
+// index that would not be much smaller than the tile table, or that finds no
+// memory, is left out: the labels then read the table.
+int ensure_label_index(raster_handle* h) {
+    if (!h->lidx_stale) return RASTER_OK;
+    h->lidx_stale = false;
+    h->lidx_on = false;
+    const long long K = h->result.n_tiles;
+    if (h->dims != 2 || h->lidx_mode < 0 || K <= 0) return RASTER_OK;
+    const double table_bytes = (double)h->cap * sizeof(Slot);
+    if (h->lidx_mode == 0 && table_bytes <= kLidxMinTableBytes) return RASTER_OK;
+    int lb = 10;  // bitmap of 2^lb bits, at least 8 per kept tile up to 32 MiB
+    while (lb < 28 && (1ull << lb) < 8ull * (unsigned long long)K) ++lb;
+    const unsigned long long words = (1ull << lb) >> 5;
+    if (words > h->lbitmap_words) {
+        if (h->lbitmap) cudaFree(h->lbitmap);
+        h->lbitmap = nullptr;
+        h->lbitmap_words = 0;
+        if (cudaMalloc(&h->lbitmap, words * 4) != cudaSuccess) {
+            cudaGetLastError();
+            h->lbitmap = nullptr;
+            return RASTER_OK;
+        }
+        h->lbitmap_words = words;
+    }
+    if (!h->d_lidx) RCHECK(h, cudaMalloc(&h->d_lidx, 2 * sizeof(unsigned long long)));
+    cudaStream_t s = h->stream;
+    RCHECK(h, cudaMemsetAsync(h->lbitmap, 0, words * 4, s));
+    RCHECK(h, cudaMemsetAsync(h->d_lidx, 0, 2 * sizeof(unsigned long long), s));
+    static int g_cnt = grid_for((const void*)k_lidx_count, kBlock);
+    static int g_zer = grid_for((const void*)k_lidx_zeros, kBlock);
+    static int g_bld = grid_for((const void*)k_lidx_build, kBlock);
+    const int lim = (int)std::max<long long>(1, (K + kBlock - 1) / kBlock);
+    k_lidx_count<<<std::min(g_cnt, lim), kBlock, 0, s>>>(h->d_ctr + 2, h->out_key, h->lbitmap, lb);
+    k_lidx_zeros<<<(int)std::min<unsigned long long>(g_zer, (words + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        h->lbitmap, words, h->d_lidx);
+    note_launch(2);
+    RCHECK(h, cudaGetLastError());
+    unsigned long long zeros = 0;
+    RCHECK(h, cudaMemcpyAsync(&zeros, h->d_lidx, sizeof(zeros), cudaMemcpyDeviceToHost, s));
+    RCHECK(h, cudaStreamSynchronize(s));
+    const double M = (double)(1ull << lb);
+    double blocks = zeros > 0 ? -M * std::log((double)zeros / M) : (double)K;
+    blocks = std::min(blocks * 1.02 + 16.0, (double)K);
+    const unsigned long long share = (unsigned long long)std::ceil(blocks / kLidxLoad / 2.0 / h->regions) + 1;
+    const unsigned long long buckets = share * h->regions;
+    if (h->lidx_mode == 0 && (double)buckets * 32.0 > 0.5 * table_bytes) return RASTER_OK;
+    if (buckets > h->lidx_alloc) {
+        if (h->lidx) cudaFree(h->lidx);
+        h->lidx = nullptr;
+        h->lidx_alloc = 0;
+        if (cudaMalloc(&h->lidx, buckets * 32) != cudaSuccess) {  // 256-byte aligned
+            cudaGetLastError();
+            h->lidx = nullptr;
+            return RASTER_OK;
+        }
+        h->lidx_alloc = buckets;
+    }
+    RCHECK(h, cudaMemsetAsync(h->lidx, 0, buckets * 32, s));
+    k_lidx_build<<<std::min(g_bld, lim), kBlock, 0, s>>>(h->d_ctr + 2, h->out_key, h->out_cid, table_of(h),
+                                                         h->lidx, buckets, share,
+                                                         reinterpret_cast<unsigned int*>(h->d_lidx + 1));
+    note_launch();
+    RCHECK(h, cudaGetLastError());
+    h->lidx_buckets = buckets;
+    h->lidx_share = share;
+    h->lidx_on = true;
+    return RASTER_OK;
+}
+
 template <bool WIDE, int DIMS>
 void launch_labels(raster_handle* h, const double* xy, long long n, int64_t* labels) {
     static int grid = grid_for((const void*)k_labels<WIDE, DIMS>, kBlock);
+    LabelIndex li{nullptr, 0, 0, nullptr};
+    if (DIMS == 2 && h->lidx_on)
+        li = LabelIndex{h->lidx, h->lidx_buckets, h->lidx_share, reinterpret_cast<unsigned int*>(h->d_lidx + 1)};
     k_labels<WIDE, DIMS><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
         xy, n, h->pp, table_of(h), h->tau, reinterpret_cast<const long long*>(h->out_cid),
-        reinterpret_cast<long long*>(labels), h->d_status);
+        reinterpret_cast<long long*>(labels), h->d_status, li);
 }
 
 template <bool WIDE, int DIMS>
@@ -666,6 +757,7 @@ int raster_create_ex(const raster_params* params, raster_handle** out) {
     h->mu = mu;
     h->groups = params->groups != 0;
     h->dims = dims;
+    if (const char* m = std::getenv("RASTER_LABEL_INDEX")) h->lidx_mode = m[0] == '0' ? -1 : m[0] == '1' ? 1 : 0;
     h->general = dims == 3 || !(params->metric == RASTER_CHEBYSHEV && params->delta == 1);
     {
         // forward half of the ball: the first nonzero offset is positive
@@ -810,13 +902,12 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     RCHECK(h, cudaGetLastError());
     static int g_init = grid_for((const void*)k_uf_init, kBlock);
     static int g_hook = grid_for((const void*)k_hook<false>, kBlock);
-    static int g_flat = grid_for((const void*)k_flatten, kBlock);
-    static int g_stat = grid_for((const void*)k_stats, kBlock);
+    static int g_flat = grid_for((const void*)k_flatten_stats, kBlock);
     static int g_emit = grid_for((const void*)k_emit, kBlock);
     const int lim = (int)std::max<long long>(1, (D + kBlock - 1) / kBlock);
     k_uf_init<<<std::min(g_init, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->csize, h->cmin);
     RCHECK(h, cudaMemsetAsync(h->d_work, 0, 8 * sizeof(unsigned long long), s));
-    const long long F = h->general ? h->nbr.n : 4;  // forward neighbours per significant tile
+    const long long F = h->general ? h->nbr.n : 1;  // threads per significant tile
     if (h->general)
         k_hook<true><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->d_nbr,
                                                                            h->nbr.n, h->dims, h->parent,
@@ -825,15 +916,14 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
         k_hook<false><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->d_nbr,
                                                                             4, 2, h->parent, h->d_work + 1,
                                                                             h->d_status);
-    k_flatten<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->d_work + 2);
     const unsigned long long order_xor = h->dims == 3 ? kOrderXor3 : kOrderXor2;
-    k_stats<<<std::min(g_stat, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->parent, h->csize, h->cmin,
-                                                     h->d_work + 3, order_xor);
+    k_flatten_stats<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->sig_key, h->csize, h->cmin,
+                                                             h->d_work + 2, order_xor);
     k_emit<<<std::min(g_emit, lim), kBlock, 0, s>>>(d_nsig, h->sig_key, h->sig_cnt, h->sig_slot, h->parent, h->csize,
                                                     h->cmin, h->mu, h->tab, h->out_key, h->out_cnt, h->out_cid,
                                                     h->out_slot, h->d_ctr + 2, h->d_ctr + 3, h->d_work + 4, order_xor,
                                                     h->dims);
-    note_launch(5);
+    note_launch(4);
     RCHECK(h, cudaGetLastError());
     rc = read_counters(h);
     if (rc) return rc;
@@ -848,6 +938,7 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     *out = h->result;
     if (hard_error(h->status)) return h->status;
     h->state = raster_handle::kAgglomerated;
+    h->lidx_stale = true;
     return h->status;
 }
 
@@ -857,6 +948,8 @@ int raster_point_labels(raster_handle* h, const double* xy, int64_t n, int64_t* 
     if (h->state != raster_handle::kAgglomerated) return RASTER_E_STATE;
     h->stream = (cudaStream_t)stream;
     if (n == 0) return RASTER_OK;
+    const int rc = ensure_label_index(h);
+    if (rc) return rc;
     if (h->dims == 3)
         h->wide ? launch_labels<true, 3>(h, xy, n, labels) : launch_labels<false, 3>(h, xy, n, labels);
     else
@@ -1121,7 +1214,7 @@ int raster_destroy(raster_handle* h) {
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
                     h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
                     h->ovf_cnt, h->d_work, h->out_slot, h->point_rr, h->row_count, h->scan_sums,
-                    h->stage2,  h->bcursor, h->d_nbr, h->res_xy};
+                    h->stage2,  h->bcursor, h->d_nbr, h->res_xy, h->lidx, h->lbitmap, h->d_lidx};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);

@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(kBlock) k_select(Slot* tab, unsigned long long
             c[it] = 0;
             bool mark = false;
             if (idx < cap) {
-                const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(tab) + idx);
+                // kept in L2: a significant slot's aux is written right after
+                const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(tab) + idx);
                 k[it] = v.x;
                 c[it] = (unsigned int)v.y;
                 mark = marked && (unsigned int)(v.y >> 32) == kAuxGroup;
@@ -128,40 +129,50 @@ struct NbrSet {
     signed char dz[kMaxFwd];
 };
 
-// One thread per (significant tile, forward neighbour); a tile's lookups and
-// unions run in parallel threads.  The default neighbourhood (Chebyshev
-// distance 1: (x+1, y-1), (x+1, y), (x+1, y+1), (x, y+1)) is specialised.
-// Significance is read from the slot: the selection wrote each significant
-// tile's row into aux, every other slot holds kAuxNone.
+// The default neighbourhood (Chebyshev distance 1: (x+1, y-1), (x+1, y),
+// (x+1, y+1), (x, y+1)) takes one thread per significant tile, which walks
+// the four in turn: fewer threads of one cluster then hook into the same
+// roots at once than with a thread per neighbour.  Other neighbourhoods (up
+// to 40 forward offsets) take one thread per (significant tile, forward
+// neighbour).  Significance is read from the slot: the selection wrote each
+// significant tile's row into aux, every other slot holds kAuxNone.
 template <bool GENERAL>
 __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
                                                 const unsigned long long* __restrict__ sig_key, RegionTable t,
                                                 const NbrSet* __restrict__ nbr, int nfwd, int dims, int* parent,
                                                 unsigned long long* work, unsigned int* d_status) {
     __shared__ long long s_chunk;
-    const int F = GENERAL ? nfwd : 4;
-    const long long SF = (long long)F * (long long)*d_nsig;
+    const long long S = (long long)*d_nsig;
     unsigned int st = 0;
+    if (!GENERAL) {
+        for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
+            const long long i = c + threadIdx.x;
+            if (i >= S) continue;
+            const unsigned long long key = sig_key[i];
+            const long long x = key_x(key), y = key_y(key);
+            for (int q = 0; q < 4; ++q) {
+                const long long nx = x + (q < 3 ? 1 : 0), ny = y + (q < 3 ? q - 1 : 1);
+                if (nx > 2147483646ll || ny > 2147483646ll || ny < -2147483647ll) continue;
+                const unsigned long long nk = pack_key((int)nx, (int)ny);
+                const Slot nb = rt_get(t, nk);
+                if (nb.key != nk || nb.aux == kAuxNone) continue;
+                if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
+            }
+        }
+        if (st) atomicOr(d_status, st);
+        return;
+    }
+    const int F = nfwd;
+    const long long SF = (long long)F * S;
     for (long long w0 = next_chunk(work, &s_chunk); w0 < SF; w0 = next_chunk(work, &s_chunk)) {
         const long long w = w0 + threadIdx.x;
         if (w >= SF) continue;
-        long long i;
-        int dx, dy, dz = 0;
-        if (GENERAL) {
-            i = w / F;
-            const int q = (int)(w - i * F);
-            dx = __ldg(&nbr->dx[q]);
-            dy = __ldg(&nbr->dy[q]);
-            dz = __ldg(&nbr->dz[q]);
-        } else {
-            i = w >> 2;
-            const int q = (int)(w & 3);
-            dx = q < 3 ? 1 : 0;
-            dy = q < 3 ? q - 1 : 1;
-        }
+        const long long i = w / F;
+        const int q = (int)(w - i * F);
+        const int dx = __ldg(&nbr->dx[q]), dy = __ldg(&nbr->dy[q]), dz = __ldg(&nbr->dz[q]);
         const unsigned long long key = sig_key[i];
         unsigned long long nk;
-        if (GENERAL && dims == 3) {
+        if (dims == 3) {
             const int nx = key3(key, 0) + dx, ny = key3(key, 1) + dy, nz = key3(key, 2) + dz;
             if (nx < kMin3 || nx > kMax3 || ny < kMin3 || ny > kMax3 || nz < kMin3 || nz > kMax3) continue;
             nk = pack_key3(nx, ny, nz);
@@ -218,16 +229,6 @@ __global__ void __launch_bounds__(kBlock) k_groups(Slot* tab, RegionTable t, uns
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_flatten(const unsigned long long* d_nsig, int* parent,
-                                                   unsigned long long* work) {
-    __shared__ long long s_chunk;
-    const long long S = (long long)*d_nsig;
-    for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
-        const long long i = c + threadIdx.x;
-        if (i < S) parent[i] = uf_root(parent, (int)i);
-    }
-}
-
 // Order of keys as unsigned integers: (x, y) order after flipping both sign
 // bits of a two-coordinate key; a three-coordinate key is in (x, y, z) order
 // as it stands.
@@ -240,17 +241,22 @@ __device__ __forceinline__ unsigned int label_code_d(unsigned long long key, uns
     return dims == 3 ? (0x80000000u | row) : label_code(key, cid, row);
 }
 
-__global__ void __launch_bounds__(kBlock) k_stats(const unsigned long long* d_nsig,
-                                                 const unsigned long long* __restrict__ sig_key,
-                                                 const int* __restrict__ parent, unsigned int* csize,
-                                                 unsigned long long* cmin, unsigned long long* work,
-                                                 unsigned long long order_xor) {
+// Root walk and component statistics in one pass: each significant tile's
+// parent becomes its root, and the root's size and smallest tile (in key
+// order) take the tile in.  Roots are final once hooking is done, and a
+// parent read while another thread rewrites it is either the old parent or
+// the root, both on the path to the same root.
+__global__ void __launch_bounds__(kBlock) k_flatten_stats(const unsigned long long* d_nsig, int* parent,
+                                                         const unsigned long long* __restrict__ sig_key,
+                                                         unsigned int* csize, unsigned long long* cmin,
+                                                         unsigned long long* work, unsigned long long order_xor) {
     __shared__ long long s_chunk;
     const long long S = (long long)*d_nsig;
     for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
         const long long i = c + threadIdx.x;
         if (i < S) {
-            const int r = parent[i];
+            const int r = uf_root(parent, (int)i);
+            parent[i] = r;
             atomicAdd(&csize[r], 1u);
             atomicMin(&cmin[r], sig_key[i] ^ order_xor);
         }
