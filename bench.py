@@ -43,7 +43,7 @@ POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 # workload, from one ncu capture with one pass per launch
 # (profiles/raster_500m_dram_per_kernel.md).  Valid only for the kernel
 # sources it was measured with; reported as null otherwise.
-MEASURED_CONTRACT_TRAFFIC = {"sources": "f170256e5f38d54f", "workload": "raster-500m", "bytes": 31_502_000_000}
+MEASURED_CONTRACT_TRAFFIC = {"sources": "290bc7ec24a37d8c", "workload": "raster-500m", "bytes": 31_499_000_000}
 
 
 def kernel_sources_digest() -> str:

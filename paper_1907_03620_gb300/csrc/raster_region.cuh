@@ -107,4 +107,16 @@ __device__ __forceinline__ Slot rt_get(const RegionTable& t, unsigned long long 
     return rt_lookup(t, key, i, load_slot(&t.tab[i]));
 }
 
+// The slot index of `key`, or -1 when it is absent.
+__device__ __forceinline__ long long rt_find(const RegionTable& t, unsigned long long key) {
+    unsigned long long i = home_slot(key, t);
+    for (unsigned int p = 0; p < t.max_probe; ++p) {
+        const unsigned long long k = t.tab[i].key;
+        if (k == key) return (long long)i;
+        if (k == kEmptyKey) return -1;
+        i = next_slot(i, t);
+    }
+    return -1;
+}
+
 }  // namespace raster

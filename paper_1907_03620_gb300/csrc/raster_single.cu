@@ -289,6 +289,18 @@ int grow_table(raster_handle* h, unsigned int regions, unsigned int bits) {
     h->regions = regions;
     h->region_bits = bits;
     h->fresh = false;  // the new table is filled
+    h->lidx_stale = true;  // its home buckets follow the regions
+    if (h->state == raster_handle::kAgglomerated && h->result.n_tiles > 0) {
+        // results are live (a reserve after the agglomeration): their slots
+        // moved, and the rehash kept no label codes
+        static int g_rst = grid_for((const void*)k_restore_rows, kBlock);
+        const int lim = (int)std::max<long long>(1, (h->result.n_tiles + kBlock - 1) / kBlock);
+        k_restore_rows<<<std::min(g_rst, lim), kBlock, 0, h->stream>>>(h->d_ctr + 2, h->out_key, h->out_cid,
+                                                                      table_of(h), h->out_slot, h->d_status);
+        note_launch();
+        RCHECK(h, cudaGetLastError());
+        RCHECK(h, cudaStreamSynchronize(h->stream));
+    }
     return RASTER_OK;
 }
 

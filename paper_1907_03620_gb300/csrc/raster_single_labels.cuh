@@ -240,6 +240,27 @@ __global__ void k_aux_codes(const unsigned long long* d_nkept, const unsigned in
         tab[out_slot[r]].aux = label_code_d(out_key[r], out_cid[r], (unsigned int)r, dims);
 }
 
+// After the table grew under live results (rehashing keeps keys and counts
+// only): each result row finds its tile's new slot, and the slot gets back
+// the row's label code.
+__global__ void k_restore_rows(const unsigned long long* d_nkept, const unsigned long long* __restrict__ out_key,
+                               const unsigned long long* __restrict__ out_cid, RegionTable t, unsigned int* out_slot,
+                               unsigned int* d_status) {
+    const long long K = (long long)*d_nkept;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned int st = 0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < K; r += stride) {
+        const long long i = rt_find(t, out_key[r]);
+        if (i < 0) {  // every kept tile was re-inserted
+            st |= kStInternal;
+            continue;
+        }
+        out_slot[r] = (unsigned int)i;
+        t.tab[i].aux = label_code_d(out_key[r], out_cid[r], (unsigned int)r, t.dims);
+    }
+    if (st) atomicOr(d_status, st);
+}
+
 constexpr unsigned long long kNoRow = ~0ull;  // a point outside every kept tile
 
 template <bool WIDE, int DIMS>

@@ -162,3 +162,34 @@ def test_small_problem_skips_the_index(monkeypatch):
     _, auto, auto_launches = labels_with(monkeypatch, None, xy, 2, 3, 2)
     assert auto_launches == on_launches - 3
     assert np.array_equal(on, auto)
+
+
+@pytest.mark.parametrize("mode", ["0", "1"])
+def test_reserve_after_agglomerate_keeps_labels_and_groups(monkeypatch, mode):
+    """Growing the table under live results (raster_reserve after the
+    agglomeration) moves every slot: the result rows find theirs again and get
+    their label codes back, and the label index is rebuilt for the new
+    regions. Labels before and after, and the RASTER' groups after, match the
+    oracle."""
+    monkeypatch.setenv("RASTER_LABEL_INDEX", mode)
+    xy = index_case(5)
+    ref, ref_lab, o = oracle.raster(xy, 2, 3, 2, with_labels=True)
+    rs_ref, idx_ref = o.point_groups(xy)
+    want = {int(k): idx_ref[rs_ref[i]:rs_ref[i + 1]] for i, k in enumerate(ref.key)}
+    d = torch.from_numpy(np.ascontiguousarray(xy)).cuda()
+    r = R.Raster(2, 3, 2)
+    r.contract(d)
+    res = r.agglomerate(allow_range_error=True)
+    assert np.array_equal(r.point_labels(d).cpu().numpy(), ref_lab)
+    cap = r.capacity
+    r.reserve(8 * cap)  # several regions where there was one
+    assert r.capacity > 4 * cap
+    assert np.array_equal(r.point_labels(d).cpu().numpy(), ref_lab)
+    row_start, idx = r.point_groups(d, res.key.numel())
+    keys = res.key.cpu().numpy().tolist()
+    rs, ix = row_start.cpu().numpy(), idx.cpu().numpy()
+    assert set(keys) == set(want)
+    for row, k in enumerate(keys):
+        assert np.array_equal(np.sort(ix[rs[row]:rs[row + 1]]), want[k]), k
+    assert np.array_equal(r.point_labels(d).cpu().numpy(), ref_lab)
+    r.close()
