@@ -206,7 +206,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "points_per_s", "value": v, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(w, args.workload),
+            "data": "synthetic", "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}"),
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {sample:,} points of the workload per step"},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
