@@ -317,7 +317,7 @@ typedef struct {
     int64_t table_slots;  /* tile-table arena, 16-byte slots (a request of n points takes a power
                              of two >= n / 0.75, at least 4096) */
     int64_t result_rows;  /* result arena rows (a request takes max(1, n / tau)) */
-    int32_t max_active;   /* most requests admitted at once */
+    int32_t max_active;   /* most requests admitted at once, 1..8192 */
 } raster_server_config;
 
 typedef struct {
@@ -383,7 +383,10 @@ int raster_server_destroy(raster_server *s);
  * calls share the array and each clears it first: calls whose GPU work
  * overlaps (other streams or host threads) race and must be serialised.
  * Returns RASTER_E_RANGE if some point was skipped (non-finite or out of the
- * int32 tile range), RASTER_E_ARG for bad arguments. */
+ * int32 tile range); the rows of every other tile are still written with
+ * their exact counts and *n_tiles_out is set, so the caller may use them.
+ * n = 0 returns RASTER_OK with *n_tiles_out = 0 (xy may then be NULL).
+ * Returns RASTER_E_ARG for bad arguments. */
 int raster_count_tiles_static(const double *xy, int64_t n, double precision, int64_t *key_out,
                               uint32_t *count_out, int64_t *n_tiles_out, void *stream);
 

@@ -388,20 +388,20 @@ void oracle_project(const double *xy, int64_t n, double scale, int64_t *keys, ui
 }
 
 /* Exact counts of a given set of tiles over a point set (one pass), used to
- * check sampled outputs of very large runs one by one. */
+ * check sampled outputs of very large runs one by one.  counts[j] is the
+ * number of points whose tile is keys[j]; a key may be queried more than
+ * once, and points with a range error count nowhere. */
 void oracle_count_keys(const double *xy, int64_t n, double scale, const int64_t *keys, int64_t k,
                        uint64_t *counts, int dims) {
-    std::unordered_map<int64_t, int64_t> where;
-    for (int64_t j = 0; j < k; ++j) {
-        where[keys[j]] = j;
-        counts[j] = 0;
-    }
+    std::unordered_map<int64_t, uint64_t> tally;
+    for (int64_t j = 0; j < k; ++j) tally[keys[j]] = 0;
     for (int64_t i = 0; i < n; ++i) {
         int64_t key;
         if (!project_point(xy, i, dims, scale, &key)) continue;
-        auto it = where.find(key);
-        if (it != where.end()) counts[it->second] += 1;
+        auto it = tally.find(key);
+        if (it != tally.end()) it->second += 1;
     }
+    for (int64_t j = 0; j < k; ++j) counts[j] = tally.at(keys[j]);
 }
 
 }  // extern "C"

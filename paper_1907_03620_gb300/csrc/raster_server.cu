@@ -224,7 +224,7 @@ bool run_step(raster_server* s) {
     {
         std::unique_lock<std::mutex> lk(s->mu);
         // 1. admission in arrival order, by free arena space
-        while (!s->waiting.empty() && (int)s->active.size() < s->max_active) {
+        while (!s->waiting.empty() && (int)s->active.size() < s->max_active && (int)fills.size() < kMaxStepItems) {
             Request* r = s->waiting.front();
             unsigned long long toff = 0, roff = 0;
             if (!s->tab_alloc.alloc(r->cap, kSlotChunk, &toff)) break;
@@ -270,9 +270,11 @@ bool run_step(raster_server* s) {
         }
         e = cudaMemcpyAsync(s->dc.fill_off, s->hc.fill_off, sizeof(unsigned long long) * nf, cudaMemcpyHostToDevice, st);
         if (!e) e = cudaMemcpyAsync(s->dc.fill_len, s->hc.fill_len, sizeof(unsigned long long) * nf, cudaMemcpyHostToDevice, st);
-        dim3 grid(64, (unsigned)std::min(nf, 1024));
-        k_fill_ranges<<<grid, 256, 0, st>>>(s->tab_arena, s->dc.fill_off, s->dc.fill_len, nf);
-        note_launch(1);
+        if (!e) {
+            dim3 grid(64, (unsigned)std::min(nf, 1024));
+            k_fill_ranges<<<grid, 256, 0, st>>>(s->tab_arena, s->dc.fill_off, s->dc.fill_len, nf);
+            note_launch(1);
+        }
     }
     const int nw = (int)work.size();
     if (!e && nw > 0) {
@@ -287,9 +289,11 @@ bool run_step(raster_server* s) {
         e = cudaMemcpyAsync(s->dc.inst, s->hc.inst, sizeof(BatchInst) * nw, cudaMemcpyHostToDevice, st);
         if (!e) e = cudaMemcpyAsync(s->dc.prefix, s->hc.prefix, sizeof(long long) * (nw + 1), cudaMemcpyHostToDevice, st);
         if (!e) e = cudaMemsetAsync(s->dc.ctr, 0, sizeof(InstCounters) * nw, st);
-        k_batch_contract<4, true><<<s->g_con, 256, 0, st>>>(s->dc.inst, s->dc.prefix, nw, s->dc.ctr);
-        if (!e) e = cudaMemcpyAsync(s->hc.ctr, s->dc.ctr, sizeof(InstCounters) * nw, cudaMemcpyDeviceToHost, st);
-        note_launch(1);
+        if (!e) {
+            k_batch_contract<4, true><<<s->g_con, 256, 0, st>>>(s->dc.inst, s->dc.prefix, nw, s->dc.ctr);
+            note_launch(1);
+            e = cudaMemcpyAsync(s->hc.ctr, s->dc.ctr, sizeof(InstCounters) * nw, cudaMemcpyDeviceToHost, st);
+        }
     }
     const int na = (int)finishing.size();
     if (!e && na > 0) {
@@ -301,6 +305,8 @@ bool run_step(raster_server* s) {
         e = cudaMemcpyAsync(s->da.inst, s->ha.inst, sizeof(BatchInst) * na, cudaMemcpyHostToDevice, st);
         if (!e) e = cudaMemcpyAsync(s->da.prefix, s->ha.prefix, sizeof(long long) * (na + 1), cudaMemcpyHostToDevice, st);
         if (!e) e = cudaMemsetAsync(s->da.ctr, 0, sizeof(InstCounters) * na, st);
+    }
+    if (!e && na > 0) {
         k_batch_select<<<s->g_sel, kScanBlock, 0, st>>>(s->da.inst, s->da.prefix, na, s->da.ctr, s->sig_key,
                                                        s->sig_cnt, s->sig_slot);
         k_batch_scan<<<1, kScanBlock, 0, st>>>(s->da.ctr, na, s->da.sprefix);
@@ -405,6 +411,7 @@ int raster_server_destroy(raster_server* s) {
 
 int raster_server_create(const raster_server_config* cfg, raster_server** out) {
     if (!cfg || !out || cfg->table_slots <= 0 || cfg->result_rows <= 0 || cfg->max_active <= 0 ||
+        cfg->max_active > kMaxStepItems ||
         cfg->table_slots > (1ll << 34) || cfg->result_rows >= 0x7FFFFFFFll)
         return RASTER_E_ARG;
     *out = nullptr;

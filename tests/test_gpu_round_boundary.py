@@ -1,11 +1,13 @@
 """More than 2^30 points in one contract call run as several contraction
 rounds: the table must be the same as for the same points given in chunks,
-and the counts must sum to n."""
+the counts must sum to n, and sampled tile counts (half of them significant
+tiles) must equal the oracle's recount over all points."""
 import numpy as np
 import pytest
 import torch
 
 import gen
+import oracle
 import paper_1907_03620_gb300 as R
 
 pytestmark = pytest.mark.gpu
@@ -17,7 +19,6 @@ def test_call_above_one_round():
     host = torch.empty((w.n, 2), dtype=torch.float64)
     gen.points_into(host.numpy(), w)
     d = host.cuda()
-    del host
     r = R.Raster(w.precision, w.tau, w.mu)
     r.contract(d)  # two rounds
     a = r.agglomerate().sorted()
@@ -33,5 +34,12 @@ def test_call_above_one_round():
     o1, o2 = np.argsort(k1), np.argsort(k2)
     assert np.array_equal(k1[o1], k2[o2]) and np.array_equal(c1[o1], c2[o2])
     assert int(c1.sum()) == w.n
+    rng = np.random.default_rng(43)
+    sig = np.flatnonzero(c1 >= w.tau)
+    sample = np.concatenate([k1[rng.choice(len(k1), 1000, replace=False)],
+                             k1[sig[rng.choice(len(sig), 1000, replace=False)]]])
+    want = oracle.count_keys(host.numpy(), oracle.scale_of(w.precision), sample)
+    got = c1[o1][np.searchsorted(k1[o1], sample)]
+    assert np.array_equal(got.astype(np.uint64), want)
     assert torch.equal(a.key, b.key) and torch.equal(a.count, b.count) and torch.equal(a.cid, b.cid)
     assert a.n_points == w.n and a.n_clusters == b.n_clusters

@@ -618,3 +618,47 @@ def test_3d_labels_and_groups():
     rs, idx = o.point_groups(xyz)
     for i, k in enumerate(r.key.tolist()):
         assert set(idx[rs[i]:rs[i + 1]].tolist()) == set(np.flatnonzero(keys == k).tolist())
+
+
+def _count_keys_reference(xy, scale, keys):
+    """Counts of the given tiles by numpy: floor of the scaled coordinates,
+    rows with a non-finite or out-of-range index dropped, then a membership
+    count per queried key."""
+    with np.errstate(invalid="ignore", over="ignore"):
+        f = np.floor(xy * scale)
+    dims = xy.shape[1]
+    lo, hi = (-(2**31 - 1), 2**31 - 2) if dims == 2 else (-(2**20 - 1), 2**20 - 2)
+    ok = np.all(np.isfinite(f) & (f >= lo) & (f <= hi), axis=1)
+    g = f[ok].astype(np.int64)
+    pk = oracle.pack(g[:, 0], g[:, 1]) if dims == 2 else oracle.pack3(g[:, 0], g[:, 1], g[:, 2])
+    uk, uc = np.unique(pk, return_counts=True)
+    i = np.minimum(np.searchsorted(uk, keys), len(uk) - 1)
+    return np.where(uk[i] == keys, uc[i], 0).astype(np.uint64)
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_count_keys_matches_numpy(dims):
+    """oracle.count_keys recounts chosen tiles over a point set (the checker of
+    the sampled large-workload tests): equal to numpy's floor + unique, with
+    range-error points mixed in, absent and duplicated query keys, and the
+    query order kept."""
+    g = np.random.default_rng(40 + dims)
+    xy = np.concatenate([g.uniform(0, 0.3, (20000, dims)), g.uniform(-2, 2, (5000, dims))])
+    bad = np.array([[np.nan] * dims, [np.inf] * dims, [-np.inf] * dims, [3.0e7] * dims, [-2.2e7] * dims])
+    xy = np.concatenate([xy, bad])[g.permutation(len(xy) + len(bad))]
+    scale = 100.0
+    keys_all, ok = oracle.project(xy, scale)
+    present = np.unique(keys_all[ok])
+    f = g.integers(-300, 300, (50, dims))
+    absent = oracle.pack(f[:, 0], f[:, 1]) if dims == 2 else oracle.pack3(f[:, 0], f[:, 1], f[:, 2])
+    q = np.concatenate([g.choice(present, 400, replace=False), absent, present[:3], present[:3]])
+    q = q[g.permutation(len(q))]
+    got = oracle.count_keys(xy, scale, q)
+    want = _count_keys_reference(xy, scale, q)
+    assert np.array_equal(got, want)
+    assert int(got[np.isin(q, present)].min()) >= 1
+    # the whole tile set recounted equals the oracle's own table
+    o = oracle.Oracle(2, 1, 1, dims=dims)
+    o.add(xy)
+    tk, tc = o.tiles()
+    assert np.array_equal(oracle.count_keys(xy, scale, tk), tc)

@@ -21,7 +21,8 @@ MUTANTS = {
     "max_id": ("if (before(s, k, cid)) cid = k;", "if (before(s, cid, k)) cid = k;"),
     "transposed_key": ("*key = pack(ix, iy);", "*key = pack(iy, ix);"),
     "single_precision_scale": ("v * scale", "v * (double)(float)scale"),
-    "lost_increment": ("it->second += 1;", "it->second += (it->second > 3) ? 0 : 1;"),
+    "lost_increment": ("        else\n            it->second += 1;",
+                       "        else\n            it->second += (it->second > 3) ? 0 : 1;"),
     "range_off_by_one": ("f <= 2147483646.0", "f <= 2147483647.0"),
     "group_window_2x1": ("for (int gy = 0; gy <= 1; ++gy)", "for (int gy = 0; gy <= 0; ++gy)"),
     "group_strict_tau": ("if (total >= s->tau) keep = true;", "if (total > s->tau) keep = true;"),
@@ -30,6 +31,15 @@ MUTANTS = {
     "delta_ignored": ("for (int dx = -s->delta; dx <= s->delta; ++dx)", "for (int dx = -1; dx <= 1; ++dx)"),
     "third_axis_ignored": ("const int dz_max = s->dims == 3 ? s->delta : 0;", "const int dz_max = 0;"),
     "third_field_shift": ("((iy + BIAS3) << 21)", "((iy + BIAS3) << 20)"),
+    "count_keys_lost_count": ("if (it != tally.end()) it->second += 1;",
+                              "if (it != tally.end()) it->second = 1;"),
+    "count_keys_counts_range_errors": ("if (!project_point(xy, i, dims, scale, &key)) continue;",
+                                       "if (!project_point(xy, i, dims, scale, &key)) key = 0;"),
+    "count_keys_two_dims": ("if (!project_point(xy, i, dims, scale, &key)) continue;",
+                            "if (!project_point(xy, i, 2, scale, &key)) continue;"),
+    "count_keys_one_slot_per_key": ("for (int64_t j = 0; j < k; ++j) counts[j] = tally.at(keys[j]);",
+                                    "for (int64_t j = 0; j < k; ++j) counts[j] = tally.at(keys[j]);\n"
+                                    " for (int64_t j = 1; j < k; ++j) if (keys[j] == keys[j - 1]) counts[j] = 0;"),
 }
 
 
@@ -95,6 +105,10 @@ def _pins_pass(lib) -> bool:
         if not (np.array_equal(r.key, bk) and np.array_equal(r.cid, bcid) and r.n_clusters == bn
                 and r.n_significant == int(sig.sum())):
             return False
+    # recounts of chosen tiles (the checker of sampled large runs) against numpy;
+    # query keys duplicated, absent, and the key 0 that a skipped point must not reach
+    if not _count_keys_pass(lib):
+        return False
     # three coordinates: counts against numpy, components against scipy (26-connectivity)
     g = np.random.default_rng(3)
     xyz = np.concatenate([g.uniform(0, 0.2, (4000, 3)), g.uniform(-1, 1, (3000, 3))])
@@ -113,6 +127,26 @@ def _pins_pass(lib) -> bool:
     _, n = ndimage.label(grid, structure=ndimage.generate_binary_structure(3, 3))
     if r.n_clusters != n:
         return False
+    return True
+
+
+def _count_keys_pass(lib) -> bool:
+    g = np.random.default_rng(11)
+    for dims in (2, 3):
+        xy = np.concatenate([g.uniform(-0.05, 0.2, (3000, dims)),
+                             np.array([[np.nan] * dims, [np.inf] * dims, [4.0e7] * dims])])
+        with np.errstate(invalid="ignore", over="ignore"):
+            f = np.floor(xy * 100.0)
+        lim = 2**31 - 2 if dims == 2 else 2**20 - 2
+        ok = np.all(np.isfinite(f) & (np.abs(f) <= lim), axis=1)
+        f = f[ok].astype(np.int64)
+        pk = oracle.pack(f[:, 0], f[:, 1]) if dims == 2 else oracle.pack3(f[:, 0], f[:, 1], f[:, 2])
+        uk, uc = np.unique(pk, return_counts=True)
+        q = np.concatenate([uk[:40], uk[39:45], np.array([0, int(oracle.pack(900, 900))], dtype=np.int64)])
+        want = np.concatenate([uc[:40], uc[39:45], [int(uc[uk == 0][0]) if (uk == 0).any() else 0, 0]])
+        got = oracle.count_keys(xy, 100.0, q, lib=lib)
+        if not np.array_equal(got, want.astype(np.uint64)):
+            return False
     return True
 
 
