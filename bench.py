@@ -38,11 +38,11 @@ import gen  # noqa: E402
 TILE_BYTES = 12          # algorithmic bytes per distinct tile (key + count written once)
 POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 
-# DRAM bytes (read + write) of one contraction phase -- k_part, k_region_items
-# and k_insert -- in a steady-state step of the 500M-point
-# workload, from one ncu capture with one pass per launch
-# (profiles/raster_500m_dram_per_kernel.md).  Valid only for the kernel
-# sources it was measured with; reported as null otherwise.
+# DRAM bytes (read + write) of one contraction phase (k_part, k_region_items,
+# k_bucket and k_insert_bucket) in a steady-state step of the 500M-point
+# workload, from one ncu capture with one pass per launch.  Valid only for the
+# kernel sources it was measured with (their digest below); reported as null
+# otherwise.
 MEASURED_CONTRACT_TRAFFIC = {"sources": "290bc7ec24a37d8c", "workload": "raster-500m", "bytes": 31_499_000_000}
 
 
@@ -67,12 +67,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="points of the oracle sample")
+    ap.add_argument("--cpu-parallel-sample", type=int, default=100_000_000,
+                    help="points of the multi-threaded P-RASTER sample")
     ap.add_argument("--profile", action="store_true", help="short run for ncu (no clocks/e2e/cpu legs)")
     ap.add_argument("--points", type=int, default=0, help="use only the first N points (profiling cases)")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served legs")
-    ap.add_argument("--loop-seconds", type=float, default=15.0, help="time budget of the single-call loop baseline")
-    ap.add_argument("--serve-seconds", type=float, default=20.0, help="duration of each Poisson serving run")
-    ap.add_argument("--serve-rates", default="0.8", help="arrival rates as fractions of saturated throughput")
+    ap.add_argument("--loop-seconds", type=float, default=8.0, help="time budget of each single-call loop baseline")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="duration of each Poisson serving run")
+    ap.add_argument("--serve-rates", default="0.5,0.8,0.95", help="arrival rates as fractions of saturated throughput")
+    ap.add_argument("--serve-pool", type=int, default=512, help="requests staged on the device for the served leg")
     return ap.parse_args()
 
 
@@ -191,6 +194,22 @@ def oracle_sample(w: gen.Workload, sample: int):
     return xy.shape[0] / dt, dt, f"first {xy.shape[0]:,} points of the workload (contract + agglomerate + labels)"
 
 
+def praster_sample(w: gen.Workload, sample: int) -> dict:
+    """Time P-RASTER (Sect. 3.5, Alg. 2-3; the oracle library's multi-threaded
+    form) on all host cores over the first `sample` points of the workload:
+    contraction (per-thread maps, join), agglomeration (slices, border joins)
+    and labels."""
+    import oracle
+    xy = gen.points(w, 0, min(sample, w.n))
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res, _, secs = oracle.praster(xy, w.precision, w.tau, w.mu, threads, with_labels=True)
+    dt = time.perf_counter() - t0
+    return {"value": xy.shape[0] / dt, "unit": "points/s", "cores": threads, "kind": "P-RASTER (oracle library)",
+            "sample": f"first {xy.shape[0]:,} points of the workload (contract + agglomerate + labels)",
+            "seconds": dt, "phases_s": secs}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     w = gen.NAMED[args.workload]
@@ -208,12 +227,57 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}"),
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample:,} points of the workload per step"},
+                             "sample": f"first {sample:,} points of the workload per step",
+                             "host_cores": os.cpu_count()},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
+
+def single_call_loops(items, seconds: float) -> dict:
+    """Two loops of plain single-instance calls over the same instances, each
+    time-bounded, one instance at a time with a synchronisation after each:
+    `reuse` keeps one handle per (precision, tau, mu) and resets it between
+    instances (raster_reset); `create` creates and destroys a handle per
+    instance.  items: (xy or list of chunk views, precision, tau, mu, chunks)."""
+    import torch
+
+    import paper_1907_03620_gb300 as R
+    out = {}
+    for mode in ("reuse", "create"):
+        handles = {}
+        lat, pts = [], 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for xy, p, tau, mu, _ in items:
+            views = xy if isinstance(xy, list) else [xy]
+            t1 = time.perf_counter()
+            if mode == "reuse":
+                h = handles.get((p, tau, mu))
+                if h is None:
+                    h = handles[(p, tau, mu)] = R.Raster(p, tau, mu)
+                h.reset()
+            else:
+                h = R.Raster(p, tau, mu)
+            for v in views:
+                h.contract(v)
+            h.agglomerate(copy=False, raw=True)
+            if mode == "create":
+                h.close()
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - t1) * 1e3)
+            pts += sum(int(v.shape[0]) for v in views)
+            if time.perf_counter() - t0 > seconds:
+                break
+        for h in handles.values():
+            h.close()
+        out[mode] = {"value": pts / (sum(lat) / 1e3), "unit": "points/s", "instances": len(lat), "points": pts,
+                     "latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
+                     "calls": ("one handle per (p, tau, mu): reset, contract per chunk, agglomerate" if mode == "reuse"
+                               else "create, contract per chunk, agglomerate, destroy")}
+    return out
+
 
 def batched_leg(args, dev):
     """Batched form: the 4096-instance workload in one graph launch, against a
@@ -255,23 +319,9 @@ def batched_leg(args, dev):
     n_clusters = sum(b.counts(i).n_clusters for i in range(len(ws)))
     dev_bytes = b.device_bytes
     b.close()
-    # loop of plain single-instance calls, time-bounded, over a fixed order
-    lat, pts = [], 0
-    order = list(range(len(ws)))
-    t_loop0 = time.perf_counter()
-    torch.cuda.synchronize()
-    for i in order:
-        t1 = time.perf_counter()
-        r = R.Raster(ws[i].precision, ws[i].tau, ws[i].mu)
-        r.contract(inst[i][0])
-        r.agglomerate(copy=False)
-        r.close()
-        torch.cuda.synchronize()
-        lat.append((time.perf_counter() - t1) * 1e3)
-        pts += ws[i].n
-        if time.perf_counter() - t_loop0 > args.loop_seconds:
-            break
-    loop_rate = pts / (sum(lat) / 1e3)
+    loops = single_call_loops([(inst[i][0], ws[i].precision, ws[i].tau, ws[i].mu, 1) for i in range(len(ws))],
+                              args.loop_seconds)
+    best = max(loops.values(), key=lambda v: v["value"])
     del flat
     torch.cuda.empty_cache()
     q = lambda v, p: float(np.percentile(np.array(v), p))  # noqa: E731
@@ -280,30 +330,39 @@ def batched_leg(args, dev):
             "latency_p50_ms": q(times, 50), "latency_p99_ms": q(times, 99),
             "clusters": n_clusters, "device_bytes": dev_bytes, "config": cfg, "tune_seconds": tune_s,
             "gpu_launches_per_run": launches_per_run,
-            "loop_baseline": {"value": loop_rate, "unit": "points/s", "instances": len(lat), "points": pts,
-                              "latency_p50_ms": q(lat, 50), "latency_p99_ms": q(lat, 99),
-                              "calls": "create, contract, agglomerate, destroy per instance"},
-            "speedup_vs_loop": (total / (ms / 1e3)) / loop_rate}
+            "loop_baseline": loops,
+            "speedup_vs_loop": (total / (ms / 1e3)) / best["value"],
+            "speedup_vs_loop_against": best["calls"]}
 
 
 def served_leg(args, dev):
-    """Served form: Poisson arrivals of requests (sizes log-uniform 1e4..2e7,
-    1..8 chunks each, per-request p/tau/mu) into the continuous-batching
-    engine.  Request data comes from a pool of pre-staged device workloads."""
+    """Served form: Poisson arrivals of requests into the continuous-batching
+    engine for --serve-seconds at each rate in --serve-rates (fractions of the
+    saturated throughput).  Requests follow the serving workload: sizes
+    log-uniform in [1e4, 2e7), 1..8 chunks, per-request p/tau/mu.  Their points
+    come from a pool of --serve-pool requests drawn from that distribution and
+    staged on the device (arrival k takes a pseudo-random pool entry), since
+    60 s of arrivals would be terabytes of input."""
     import torch
 
-    import paper_1907_03620_gb300 as R
     from paper_1907_03620_gb300.serve import RasterServer
 
-    pool_n = 48
+    pool_n = args.serve_pool
+    ws = [gen._instance(5, i, gen._log_uniform_size(5, i, 10_000, 20_000_000), 0.10) for i in range(pool_n)]
+    nchunks = [int(1 + gen.rng_at(5, 15, i) % 8) for i in range(pool_n)]
+    offs = np.cumsum([0] + [w.n for w in ws])
+    flat = torch.empty((int(offs[-1]), 2), dtype=torch.float64, device=dev)
+    stage = torch.empty((max(w.n for w in ws), 2), dtype=torch.float64, pin_memory=True)
+    for i, w in enumerate(ws):
+        gen.points_into(stage[: w.n].numpy(), w)
+        flat[offs[i]:offs[i + 1]].copy_(stage[: w.n])
+    del stage
     pool = []
-    for i in range(pool_n):
-        w = gen._instance(5, i, gen._log_uniform_size(5, i, 10_000, 20_000_000), 0.10)
-        chunks = 1 + gen.rng_at(5, 15, i) % 8
-        xy = torch.from_numpy(gen.points(w)).to(dev)
-        views = [xy[lo:hi] for lo, hi in gen.chunk_bounds(w.n, int(chunks))]
-        pool.append((w, xy, views))
-    srv = RasterServer(table_slots=1 << 32, result_rows=1 << 28, max_active=4096)
+    for i, w in enumerate(ws):
+        xy = flat[offs[i]:offs[i + 1]]
+        pool.append((w, [xy[lo:hi] for lo, hi in gen.chunk_bounds(w.n, nchunks[i])]))
+    mean_pts = float(offs[-1]) / pool_n
+    srv = RasterServer(max_active=4096, reserve_bytes=8 << 30)
     done_lat, done_pts = [], [0]
     lock = threading.Lock()
     stop = [False]
@@ -320,99 +379,79 @@ def served_leg(args, dev):
                 done_pts[0] += res.n_points
 
     def submit(rid, k):
-        w, xy, views = pool[k % pool_n]
+        w, views = pool[k]
         srv.submit(rid, w.precision, w.tau, w.mu, w.n, len(views))
         for v in views:
             srv.push(rid, v)
 
+    def wait_done(count):
+        while True:
+            with lock:
+                if len(done_lat) >= count:
+                    return
+            time.sleep(0.002)
+
+    def take():
+        with lock:
+            lat, pts = list(done_lat), done_pts[0]
+            done_lat.clear()
+            done_pts[0] = 0
+        return lat, pts
+
     th = threading.Thread(target=poller, daemon=True)
     th.start()
-    # saturation: a burst of requests submitted at once
-    burst = 4 * pool_n
-    for k in range(pool_n):  # warm-up pass
+    for k in range(min(pool_n, 64)):  # warm-up
         submit(10**9 + k, k)
-    while True:
-        with lock:
-            if len(done_lat) >= pool_n:
-                break
-        time.sleep(0.01)
-    with lock:
-        done_lat.clear()
-        done_pts[0] = 0
+    wait_done(min(pool_n, 64))
+    take()
+    # saturation: the whole pool submitted at once
     t0 = time.perf_counter()
-    for k in range(burst):
+    for k in range(pool_n):
         submit(k, k)
-    while True:
-        with lock:
-            if len(done_lat) >= burst:
-                break
-        time.sleep(0.002)
+    wait_done(pool_n)
     t_sat = time.perf_counter() - t0
-    with lock:
-        sat_pts = done_pts[0]
-        done_lat.clear()
-        done_pts[0] = 0
+    _, sat_pts = take()
     sat_rate = sat_pts / t_sat
-    mean_pts = sat_pts / burst
     runs = []
     rid = 10**6
+    peak_bytes = 0
     for frac in [float(f) for f in args.serve_rates.split(",") if f]:
         req_rate = frac * sat_rate / mean_pts
         arrivals = gen.serve_requests(rate_per_s=req_rate, duration_s=args.serve_seconds, seed=7)
-        with lock:
-            done_lat.clear()
-            done_pts[0] = 0
+        picks = [int(gen.rng_at(7, 16, k) % pool_n) for k in range(len(arrivals))]
         t0 = time.perf_counter()
         for k, rq in enumerate(arrivals):
             delay = rq.arrival_s - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            submit(rid, k)
+            submit(rid, picks[k])
             rid += 1
-        while True:
-            with lock:
-                if len(done_lat) >= len(arrivals):
-                    break
-            time.sleep(0.002)
+            if k % 256 == 0:
+                peak_bytes = max(peak_bytes, srv.stats()["device_bytes"])
+        wait_done(len(arrivals))
         wall = time.perf_counter() - t0
-        with lock:
-            lat = list(done_lat)
-            pts = done_pts[0]
+        lat, pts = take()
         runs.append({"load_fraction": frac, "requests": len(arrivals), "offered_req_per_s": req_rate,
-                     "points_per_s": pts / wall, "latency_p50_ms": float(np.percentile(lat, 50)),
-                     "latency_p99_ms": float(np.percentile(lat, 99)), "seconds": wall})
+                     "offered_points_per_s": frac * sat_rate, "points_per_s": pts / wall,
+                     "latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
+                     "seconds": wall})
     stop[0] = True
     th.join()
     st = srv.stats()
     srv.close()
-    # FIFO loop of plain single-instance calls over the same request mix
-    loop_lat, loop_pts = [], 0
-    t_loop = time.perf_counter()
-    k = 0
-    while time.perf_counter() - t_loop < args.loop_seconds and k < 4 * pool_n:
-        w, xy, views = pool[k % pool_n]
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        h = R.Raster(w.precision, w.tau, w.mu)
-        for v in views:
-            h.contract(v)
-        h.agglomerate(copy=False)
-        h.close()
-        torch.cuda.synchronize()
-        loop_lat.append((time.perf_counter() - t1) * 1e3)
-        loop_pts += w.n
-        k += 1
-    loop_rate = loop_pts / (sum(loop_lat) / 1e3)
-    del pool
+    loops = single_call_loops([(views, w.precision, w.tau, w.mu, len(views)) for w, views in pool],
+                              args.loop_seconds)
+    best = max(loops.values(), key=lambda v: v["value"])
+    del pool, flat
     torch.cuda.empty_cache()
-    return {"metric": "points_per_s", "saturated_points_per_s": sat_rate, "saturated_burst_requests": burst,
+    return {"metric": "points_per_s", "saturated_points_per_s": sat_rate, "saturated_burst_requests": pool_n,
             "mean_request_points": mean_pts, "runs": runs, "engine_steps": st["steps"],
-            "loop_baseline": {"value": loop_rate, "unit": "points/s", "requests": len(loop_lat),
-                              "latency_p50_ms": float(np.percentile(loop_lat, 50)),
-                              "latency_p99_ms": float(np.percentile(loop_lat, 99)),
-                              "calls": "FIFO: create, contract per chunk, agglomerate, destroy per request"},
-            "speedup_vs_loop": sat_rate / loop_rate,
-            "request_data": f"pool of {pool_n} pre-staged device workloads, request k uses pool[k % {pool_n}]"}
+            "engine_peak_device_bytes": peak_bytes, "admission": "free device memory less an 8 GiB reserve",
+            "loop_baseline": loops, "speedup_vs_loop": sat_rate / best["value"],
+            "speedup_vs_loop_per_run": {str(r["load_fraction"]): r["points_per_s"] / best["value"] for r in runs},
+            "speedup_vs_loop_against": best["calls"],
+            "request_data": (f"pool of {pool_n} requests drawn from the serving workload's distribution, staged on "
+                             f"the device; arrival k uses a pseudo-random pool entry")}
 
 
 def run_gpu(args):
@@ -651,17 +690,23 @@ def run_gpu(args):
 
         e2e_step()
         torch.cuda.synchronize()
-        # the machine's host link, for context: 2 GB of points in, 1 GB of labels out
+        # the machine's host link, for context: 2 GB of points in and 1 GB of labels
+        # out on a copy stream, timed with CUDA events on that stream, best of 3
         q = w.n // 4
+        cs = torch.cuda.Stream()
+        link = {"h2d": 0.0, "d2h": 0.0}
+        with torch.cuda.stream(cs):
+            for _ in range(3):
+                for name, dst, src, nbytes in (("h2d", xy[:q], host[:q], POINT_BYTES * q),
+                                               ("d2h", lab_host[:q], labels[:q], 8 * q)):
+                    a0, a1 = ev(), ev()
+                    a0.record(cs)
+                    dst.copy_(src, non_blocking=True)
+                    a1.record(cs)
+                    a1.synchronize()
+                    link[name] = max(link[name], nbytes / (a0.elapsed_time(a1) / 1e3) / 1e9)
+        h2d_gbs, d2h_gbs = link["h2d"], link["d2h"]
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        xy[:q].copy_(host[:q], non_blocking=True)
-        torch.cuda.synchronize()
-        h2d_gbs = POINT_BYTES * q / (time.perf_counter() - t0) / 1e9
-        t0 = time.perf_counter()
-        lab_host[:q].copy_(labels[:q], non_blocking=True)
-        torch.cuda.synchronize()
-        d2h_gbs = 8 * q / (time.perf_counter() - t0) / 1e9
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
@@ -678,7 +723,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile:
         rate, dt, desc = oracle_sample(w, args.cpu_sample)
         line["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
-                                "sample": desc, "seconds": dt}
+                                "sample": desc, "seconds": dt, "host_cores": os.cpu_count(),
+                                "parallel": praster_sample(w, args.cpu_parallel_sample)}
 
     r.close()
     del xy, labels, host

@@ -243,6 +243,19 @@ int64_t raster_table_capacity(const raster_handle *h);
  * no counterpart in the paper. */
 uint64_t raster_kernel_launches(void);
 
+/* Bounds of the device loops, lowered so that tests can drive the failure
+ * paths without faulting a GPU.  No counterpart in the paper.  probe_limit
+ * caps the slots one table insertion probes; union_limit caps the steps of
+ * one union-find join; a negative value restores the library's own bound
+ * (the default).  Lookups keep their full bound, so a lowered limit makes an
+ * insertion or a join give up, never hides a tile.  The values are read when
+ * a handle (raster_create*), a batch (raster_batch_create) or a served
+ * request (raster_server_submit) is created and stay with it; every loop
+ * still ends, and an exhausted bound surfaces as RASTER_E_TABLE_FULL or
+ * RASTER_E_INTERNAL from that handle, batch instance or request only.
+ * Process-wide; not meant for production use.  Returns RASTER_OK. */
+int raster_set_test_limits(int32_t probe_limit, int32_t union_limit);
+
 /* Release the handle and its device memory (synchronises).  Lifecycle call;
  * no counterpart in the paper. */
 int raster_destroy(raster_handle *h);
@@ -306,32 +319,47 @@ int raster_batch_destroy(raster_batch *b);
  * A serving engine with a worker thread.  Requests (one Alg. 1 problem each)
  * arrive at any time and send their points in chunks (chunked processing,
  * Sect. 3.6).  Every step the engine admits waiting requests in arrival order
- * while its device arenas can hold the request's tile table and result rows,
- * contracts every ready chunk of every admitted request in one segmented
- * launch, and agglomerates every request whose chunks are all in.  Requests
- * therefore overlap on the device; each result equals that of a separate
- * handle. */
+ * while free device memory (cudaMemGetInfo minus the caller's reserve) covers
+ * what the request's tile table and result rows add, contracts every ready
+ * chunk of every admitted request in one segmented launch, and agglomerates
+ * every request whose chunks are all in.  Requests therefore overlap on the
+ * device; each result equals that of a separate handle.
+ *
+ * Memory: tables and rows live in device address ranges reserved at create
+ * and backed by physical pages only while a live request uses them.  A
+ * request's table (a power of two >= n / 0.75 slots, at least 4096; 16 bytes
+ * each) is held from admission until it completes, its result rows
+ * (max(1, n / tau), 52 bytes each with the agglomeration's work rows) until
+ * the client releases it.  Pages no request holds are kept for reuse and
+ * given back when admission needs the memory or the engine has been idle for
+ * 0.2 s.  A request that does not fit while no other request is active is
+ * completed at once with RASTER_E_OOM. */
 typedef struct raster_server raster_server;
 
 typedef struct {
-    int64_t table_slots;  /* tile-table arena, 16-byte slots (a request of n points takes a power
-                             of two >= n / 0.75, at least 4096) */
-    int64_t result_rows;  /* result arena rows (a request takes max(1, n / tau)) */
-    int32_t max_active;   /* most requests admitted at once, 1..8192 */
+    int64_t table_slots;   /* most tile-table slots held at once; 0: as many as device memory could hold */
+    int64_t result_rows;   /* most result rows held at once; 0: as many as device memory could hold
+                              (at most 2^31 - 2) */
+    int32_t max_active;    /* most requests admitted at once, 1..8192 */
+    int64_t reserve_bytes; /* device memory admission leaves free for other users (>= 0) */
 } raster_server_config;
 
 typedef struct {
     int64_t steps, points, waiting, active, completed_unpolled, table_slots_used, result_rows_used;
+    int64_t device_bytes;  /* physical device memory the engine's tables and rows hold now */
+    int64_t refused;       /* requests completed with RASTER_E_OOM */
 } raster_server_stats_t;
 
-/* Allocate the arenas on the current device and start the worker thread.
- * RASTER_E_ARG for a bad config, RASTER_E_OOM if the arenas do not fit.
+/* Reserve the address ranges on the current device and start the worker
+ * thread; no table or row memory is committed yet.  RASTER_E_ARG for a bad
+ * config, RASTER_E_CUDA if the device lacks the virtual memory calls.
  * Lifecycle call; no counterpart in the paper. */
 int raster_server_create(const raster_server_config *cfg, raster_server **out);
 
 /* Announce request `request_id` (unique among live requests): an Alg. 1
  * problem of n_total points in n_chunks chunks.  Returns RASTER_E_LIMIT if it
- * could never fit the arenas.  Thread-safe. */
+ * could never fit (its table and rows exceed the configured bounds, or the
+ * device's memory less the reserve).  Thread-safe. */
 int raster_server_submit(raster_server *s, int64_t request_id, double precision, uint32_t tau, uint32_t mu,
                          int64_t n_total, int32_t n_chunks);
 

@@ -56,12 +56,14 @@ class BatchConfig(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
-    _fields_ = [("table_slots", ctypes.c_int64), ("result_rows", ctypes.c_int64), ("max_active", ctypes.c_int32)]
+    _fields_ = [("table_slots", ctypes.c_int64), ("result_rows", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("reserve_bytes", ctypes.c_int64)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("steps", "points", "waiting", "active", "completed_unpolled",
-                                              "table_slots_used", "result_rows_used")]
+                                              "table_slots_used", "result_rows_used", "device_bytes",
+                                              "refused")]
 
 
 class Clusters(ctypes.Structure):
@@ -104,6 +106,7 @@ def _declare(L):
         "raster_table_capacity": (i64, [vp]),
         "raster_destroy": (ci, [vp]),
         "raster_kernel_launches": (ctypes.c_uint64, []),
+        "raster_set_test_limits": (ci, [ctypes.c_int32, ctypes.c_int32]),
         "raster_count_tiles_static": (ci, [vp, i64, dbl, vp, vp, ctypes.POINTER(i64), vp]),
         "raster_strerror": (ctypes.c_char_p, [ci]),
         "raster_batch_create": (ci, [ctypes.POINTER(Instance), ctypes.c_int32, ctypes.POINTER(BatchConfig),

@@ -183,6 +183,7 @@ int raster_batch_create(const raster_instance* inst, int32_t count, const raster
     std::vector<unsigned long long> tab_off(count, 0);
     long long rows = 0;
     unsigned long long slots = 0;
+    const TestLimits lim = test_limits();
     for (int i = 0; i < count; ++i) {
         const raster_instance& r = inst[i];
         if (r.n < 0 || r.n > 0xFFFFFFFFll || r.tau == 0 || r.mu == 0 || !std::isfinite(r.precision) ||
@@ -208,6 +209,9 @@ int raster_batch_create(const raster_instance* inst, int32_t count, const raster
             return RASTER_E_ARG;
         }
         I.mask = (unsigned int)(cap - 1);
+        I.max_probe = lim.probe >= 0 ? (unsigned int)std::min<unsigned long long>((unsigned long long)lim.probe, cap)
+                                     : (unsigned int)cap;
+        I.union_limit = lim.unions >= 0 ? lim.unions : (1 << 30);
         tab_off[i] = slots;
         slots += cap;
         const long long rc = std::max<long long>(1, r.n / (long long)r.tau);

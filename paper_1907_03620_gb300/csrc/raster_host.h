@@ -17,4 +17,13 @@ double scale_of_precision(double precision);
 // Count k kernel launches issued by this library (diagnostics).
 void note_launch(unsigned long long k = 1);
 
+// Bounds of the device loops chosen for tests of the failure paths
+// (raster_set_test_limits); negative means the library's own bound.  Read
+// when a handle, batch or served request is created.
+struct TestLimits {
+    int probe;   // most slots one insertion probes
+    int unions;  // most steps of one union-find join
+};
+TestLimits test_limits();
+
 }  // namespace raster

@@ -30,6 +30,8 @@ struct BatchInst {
     unsigned int wide;
     unsigned int tau, mu;
     long long row_off;  // first row of this instance in the sig/result arenas
+    unsigned int max_probe;  // most slots one insertion probes (the table size, unless a test lowers it)
+    int union_limit;         // most steps of one union-find join
 };
 
 struct InstCounters {
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(512) k_batch_contract(const BatchInst* __restr
                     c_add = (lane == __ffs(grp) - 1 && key != kInvalidKey) ? (unsigned int)__popc(grp) : 0u;
                 }
                 if (c_add) {
-                    const int r = table_add(I.tab, I.mask, key, c_add, I.mask + 1u);
+                    const int r = table_add(I.tab, I.mask, key, c_add, I.max_probe);
                     if (r > 0)
                         ++newk;
                     else if (r < 0)
@@ -229,7 +231,7 @@ __global__ void k_batch_hook(const BatchInst* __restrict__ inst, const long long
             if (nk[q] == kInvalidKey) continue;
             const Slot nb = table_find_from(tab, mask, nk[q], ns[q], sl[q], mask + 1u);
             if (nb.key != nk[q] || nb.count < tau) continue;
-            if (!uf_unite(parent, (int)rr.row, (int)nb.aux, 1 << 30))
+            if (!uf_unite(parent, (int)rr.row, (int)nb.aux, I.union_limit))
                 atomicOr(&ctr[rr.inst].status, (unsigned long long)kStInternal);
         }
     }

@@ -3,16 +3,20 @@
 // Clients submit requests (precision, tau, mu, total points, number of chunks)
 // and push their chunks (device pointers) whenever they have them.  A worker
 // thread runs steps.  Each step:
-//   1. admits waiting requests in arrival order while the device arenas can
-//      hold the request's tile table (>= n / 0.75 slots, so it cannot
-//      overflow) and its result rows (n / tau): admission by free memory;
+//   1. admits waiting requests in arrival order while free device memory
+//      (cudaMemGetInfo, minus a reserve the caller sets) covers the pages the
+//      request's tile table (>= n / 0.75 slots, so it cannot overflow) and its
+//      result rows (n / tau) would add: admission by free HBM.  Tables and rows
+//      live in address ranges reserved once and backed page by page, so the
+//      engine holds only the memory of live requests;
 //   2. launches ONE segmented contraction over every ready chunk of every
 //      admitted request (each chunk adds into its own request's resident
 //      table);
 //   3. launches ONE segmented agglomeration (select, scan, union-find hooking,
 //      flatten, stats, emit) for every request whose chunks are all in;
-//   4. waits for the step, records completions and frees nothing until the
-//      client releases a finished request.
+//   4. waits for the step and records completions; a finished request's
+//      table pages are given back at once, its rows when the client releases
+//      it.
 // Requests that arrive while others run join the next step, so the work of
 // many requests overlaps on the device; each request's result is exactly that
 // of a separate handle (its table and rows are private to it).
@@ -35,6 +39,7 @@
 #include "../../include/raster.h"
 #include "raster_host.h"
 #include "raster_segmented.cuh"
+#include "raster_vmm.h"
 
 using namespace raster;
 
@@ -127,7 +132,10 @@ struct Request {
     enum State { kWaiting, kActive, kDone } state = kWaiting;
     unsigned long long tab_off = 0, cap = 0;
     unsigned long long row_off = 0, rows = 0;
+    bool has_table = false, has_rows = false;  // ranges held in the arrays
     unsigned long long tiles = 0, status = 0;
+    unsigned int max_probe = 0;  // probe bound of its table (its size unless a test lowered it)
+    int union_limit = 1 << 30;
     InstCounters result{};
     Clock::time_point t_submit, t_done;
 };
@@ -158,6 +166,11 @@ struct HostStep {
 struct raster_server {
     int device = 0;
     cudaStream_t stream = nullptr;
+    VmDriver drv;
+    // tile tables (16-byte slots) and the nine row arrays, each an address
+    // range backed page by page
+    VmArray tab_va;
+    VmArray row_va[9];
     Slot* tab_arena = nullptr;
     long long row_capacity = 0;
     unsigned long long* sig_key = nullptr;
@@ -171,6 +184,8 @@ struct raster_server {
     unsigned long long* out_cid = nullptr;
     RangeAllocator tab_alloc, row_alloc;
     int max_active = 0;
+    size_t reserve = 0;        // device memory admission leaves free
+    size_t total_mem = 0;
     DeviceStep dc, da;  // contraction and agglomeration descriptors
     HostStep hc, ha;
     int g_fill = 1, g_con = 1, g_sel = 1, g_agg = 1;
@@ -185,7 +200,7 @@ struct raster_server {
     int fatal = RASTER_OK;
     std::thread worker;
 
-    long long steps = 0, points = 0;
+    long long steps = 0, points = 0, refused = 0;
 };
 
 namespace {
@@ -205,6 +220,109 @@ void table_rows_for(long long n, unsigned int tau, unsigned long long* cap, unsi
     *rows = (unsigned long long)std::max<long long>(1, n / (long long)tau);
 }
 
+// The nine row arrays, in the order of raster_server::row_va: sig_key,
+// sig_cnt, sig_slot, parent, csize, cmin, out_key, out_cnt, out_cid.
+constexpr size_t kRowElem[9] = {8, 4, 4, 4, 4, 8, 8, 4, 8};
+constexpr size_t kRowBytes = 52;                 // their sum
+constexpr size_t kTablePage = 32ull << 20;       // bytes per page of the table array
+constexpr size_t kRowPageRows = 4ull << 20;      // rows per page of every row array
+constexpr unsigned long long kMaxRows = 0x7FFFFFFEull;  // row indices are int32 in union-find
+constexpr unsigned int kStOom = 8u;             // host-side status bit: refused for device memory
+constexpr double kIdleTrimMs = 200.0;           // idle this long: give cached pages back
+
+size_t free_device_memory() {
+    size_t f = 0, t = 0;
+    if (cudaMemGetInfo(&f, &t) != cudaSuccess) return 0;
+    return f;
+}
+
+// Bytes of device memory that pinning a table range and a row range would add.
+size_t new_bytes(const raster_server* s, unsigned long long toff, unsigned long long cap, unsigned long long roff,
+                 unsigned long long rows) {
+    size_t n = s->tab_va.need(toff * sizeof(Slot), (toff + cap) * sizeof(Slot));
+    for (int a = 0; a < 9; ++a) n += s->row_va[a].need(roff * kRowElem[a], (roff + rows) * kRowElem[a]);
+    return n;
+}
+
+void unpin_rows(raster_server* s, Request* r, int arrays = 9) {
+    for (int a = 0; a < arrays; ++a) s->row_va[a].unpin(r->row_off * kRowElem[a], (r->row_off + r->rows) * kRowElem[a]);
+}
+
+// Map the pages of a request's table and rows; all or nothing.
+bool pin_request(raster_server* s, Request* r) {
+    if (s->tab_va.pin(r->tab_off * sizeof(Slot), (r->tab_off + r->cap) * sizeof(Slot)) != CUDA_SUCCESS) return false;
+    for (int a = 0; a < 9; ++a) {
+        if (s->row_va[a].pin(r->row_off * kRowElem[a], (r->row_off + r->rows) * kRowElem[a]) != CUDA_SUCCESS) {
+            unpin_rows(s, r, a);
+            s->tab_va.unpin(r->tab_off * sizeof(Slot), (r->tab_off + r->cap) * sizeof(Slot));
+            return false;
+        }
+    }
+    return true;
+}
+
+void free_table(raster_server* s, Request* r) {
+    if (!r->has_table) return;
+    s->tab_va.unpin(r->tab_off * sizeof(Slot), (r->tab_off + r->cap) * sizeof(Slot));
+    s->tab_alloc.release(r->tab_off, r->cap);
+    r->has_table = false;
+}
+
+void free_rows(raster_server* s, Request* r) {
+    if (!r->has_rows) return;
+    unpin_rows(s, r);
+    s->row_alloc.release(r->row_off, r->rows);
+    r->has_rows = false;
+}
+
+size_t trim_all(raster_server* s) {
+    size_t n = s->tab_va.trim();
+    for (auto& a : s->row_va) n += a.trim();
+    return n;
+}
+
+size_t mapped_bytes(const raster_server* s) {
+    size_t n = s->tab_va.mapped_bytes();
+    for (const auto& a : s->row_va) n += a.mapped_bytes();
+    return n;
+}
+
+// Admit the oldest waiting request if free device memory covers what it
+// adds: 1 admitted, 0 it must wait, -1 it was refused (it could not fit even
+// with no other request on the device).
+int admit_front(raster_server* s) {
+    Request* r = s->waiting.front();
+    unsigned long long toff = 0, roff = 0;
+    if (!s->tab_alloc.alloc(r->cap, kSlotChunk, &toff)) return 0;
+    if (!s->row_alloc.alloc(r->rows, 1, &roff)) {
+        s->tab_alloc.release(toff, r->cap);
+        return 0;
+    }
+    r->tab_off = toff;
+    r->row_off = roff;
+    const size_t need = new_bytes(s, toff, r->cap, roff, r->rows);
+    bool ok = need == 0 || free_device_memory() >= need + s->reserve;
+    if (!ok && trim_all(s) > 0) ok = free_device_memory() >= need + s->reserve;
+    if (ok) ok = pin_request(s, r);
+    if (ok) {
+        r->has_table = r->has_rows = true;
+        return 1;
+    }
+    s->tab_alloc.release(toff, r->cap);
+    s->row_alloc.release(roff, r->rows);
+    if (!s->active.empty()) return 0;  // memory comes back as active requests finish
+    // nothing on the device will give memory back: refuse the request
+    s->waiting.pop_front();
+    r->state = Request::kDone;
+    r->result = InstCounters{};
+    r->result.status = kStOom;
+    r->t_done = Clock::now();
+    s->completed.push_back(r);
+    s->refused += 1;
+    s->cv_done.notify_all();
+    return -1;
+}
+
 BatchInst inst_of(const raster_server* s, const Request* r) {
     BatchInst I{};
     I.pp = r->pp;
@@ -214,6 +332,8 @@ BatchInst inst_of(const raster_server* s, const Request* r) {
     I.tau = r->tau;
     I.mu = r->mu;
     I.row_off = (long long)r->row_off;
+    I.max_probe = r->max_probe;
+    I.union_limit = r->union_limit;
     return I;
 }
 
@@ -223,17 +343,12 @@ bool run_step(raster_server* s) {
     std::vector<std::pair<Request*, Chunk>> work;
     {
         std::unique_lock<std::mutex> lk(s->mu);
-        // 1. admission in arrival order, by free arena space
+        // 1. admission in arrival order, by free device memory
         while (!s->waiting.empty() && (int)s->active.size() < s->max_active && (int)fills.size() < kMaxStepItems) {
+            const int a = admit_front(s);
+            if (a == 0) break;
+            if (a < 0) continue;
             Request* r = s->waiting.front();
-            unsigned long long toff = 0, roff = 0;
-            if (!s->tab_alloc.alloc(r->cap, kSlotChunk, &toff)) break;
-            if (!s->row_alloc.alloc(r->rows, 1, &roff)) {
-                s->tab_alloc.release(toff, r->cap);
-                break;
-            }
-            r->tab_off = toff;
-            r->row_off = roff;
             r->state = Request::kActive;
             s->waiting.pop_front();
             s->active.push_back(r);
@@ -344,6 +459,7 @@ bool run_step(raster_server* s) {
         r->result.status |= r->status;
         r->state = Request::kDone;
         r->t_done = now;
+        free_table(s, r);  // the rows hold the result; the table is no longer needed
         s->active.erase(std::find(s->active.begin(), s->active.end(), r));
         s->completed.push_back(r);
     }
@@ -355,20 +471,30 @@ bool run_step(raster_server* s) {
 
 void worker_main(raster_server* s) {
     cudaSetDevice(s->device);
+    Clock::time_point busy = Clock::now();
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (s->stop || s->fatal) return;
         }
-        if (!run_step(s)) {
+        if (run_step(s)) {
+            busy = Clock::now();
+        } else {
             std::unique_lock<std::mutex> lk(s->mu);
             if (s->stop || s->fatal) return;
+            // idle for a while: give the pages no live request holds back to
+            // the device (no kernel of the engine is running now)
+            if (std::chrono::duration<double, std::milli>(Clock::now() - busy).count() > kIdleTrimMs) {
+                trim_all(s);
+                busy = Clock::now();
+            }
             s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
         }
     }
 }
 
 int status_bits_to_code(unsigned long long bits) {
+    if (bits & kStOom) return RASTER_E_OOM;
     if (bits & kStInternal) return RASTER_E_INTERNAL;
     if (bits & kStFull) return RASTER_E_TABLE_FULL;
     if (bits & kStRange) return RASTER_E_RANGE;
@@ -393,16 +519,16 @@ int raster_server_destroy(raster_server* s) {
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     if (s->stream) cudaStreamSynchronize(s->stream);
-    void* bufs[] = {s->tab_arena, s->sig_key,  s->sig_cnt,      s->sig_slot,     s->parent,       s->csize,
-                    s->cmin,      s->out_key,  s->out_cnt,      s->out_cid,      s->dc.inst,      s->dc.prefix,
-                    s->dc.ctr,    s->dc.sprefix, s->dc.fill_off, s->dc.fill_len, s->da.inst,      s->da.prefix,
-                    s->da.ctr,    s->da.sprefix, s->da.fill_off, s->da.fill_len};
+    void* bufs[] = {s->dc.inst, s->dc.prefix, s->dc.ctr,      s->dc.sprefix, s->dc.fill_off, s->dc.fill_len,
+                    s->da.inst, s->da.prefix, s->da.ctr,      s->da.sprefix, s->da.fill_off, s->da.fill_len};
     for (void* p : bufs)
         if (p) cudaFree(p);
     void* hbufs[] = {s->hc.inst, s->hc.prefix, s->hc.ctr, s->hc.fill_off, s->hc.fill_len,
                      s->ha.inst, s->ha.prefix, s->ha.ctr, s->ha.fill_off, s->ha.fill_len};
     for (void* p : hbufs)
         if (p) cudaFreeHost(p);
+    s->tab_va.destroy();
+    for (auto& a : s->row_va) a.destroy();
     if (s->stream) cudaStreamDestroy(s->stream);
     for (auto& kv : s->reqs) delete kv.second;
     delete s;
@@ -410,28 +536,30 @@ int raster_server_destroy(raster_server* s) {
 }
 
 int raster_server_create(const raster_server_config* cfg, raster_server** out) {
-    if (!cfg || !out || cfg->table_slots <= 0 || cfg->result_rows <= 0 || cfg->max_active <= 0 ||
-        cfg->max_active > kMaxStepItems ||
-        cfg->table_slots > (1ll << 34) || cfg->result_rows >= 0x7FFFFFFFll)
+    if (!cfg || !out || cfg->table_slots < 0 || cfg->result_rows < 0 || cfg->max_active <= 0 ||
+        cfg->max_active > kMaxStepItems || cfg->reserve_bytes < 0 || cfg->table_slots > (1ll << 36) ||
+        cfg->result_rows > (long long)kMaxRows)
         return RASTER_E_ARG;
     *out = nullptr;
     raster_server* s = new (std::nothrow) raster_server();
     if (!s) return RASTER_E_OOM;
     cudaGetDevice(&s->device);
     s->max_active = cfg->max_active;
-    s->row_capacity = cfg->result_rows;
-    const size_t rows = (size_t)cfg->result_rows;
+    s->reserve = (size_t)cfg->reserve_bytes;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (!e) e = dmal(&s->tab_arena, (size_t)cfg->table_slots);
-    if (!e) e = dmal(&s->sig_key, rows);
-    if (!e) e = dmal(&s->sig_cnt, rows);
-    if (!e) e = dmal(&s->sig_slot, rows);
-    if (!e) e = dmal(&s->parent, rows);
-    if (!e) e = dmal(&s->csize, rows);
-    if (!e) e = dmal(&s->cmin, rows);
-    if (!e) e = dmal(&s->out_key, rows);
-    if (!e) e = dmal(&s->out_cnt, rows);
-    if (!e) e = dmal(&s->out_cid, rows);
+    size_t free_b = 0;
+    if (!e) e = cudaMemGetInfo(&free_b, &s->total_mem);
+    if (!e && !s->drv.load()) e = cudaErrorNotSupported;
+    // address ranges: as many slots and rows as the device could ever hold
+    // (or the caller's bounds); no physical memory yet
+    const unsigned long long slots =
+        cfg->table_slots > 0 ? (unsigned long long)cfg->table_slots : s->total_mem / sizeof(Slot);
+    const unsigned long long rows =
+        cfg->result_rows > 0 ? (unsigned long long)cfg->result_rows : std::min<unsigned long long>(kMaxRows, s->total_mem / kRowBytes);
+    if (!e && !s->tab_va.init(&s->drv, s->device, slots * sizeof(Slot), kTablePage)) e = cudaErrorMemoryAllocation;
+    for (int a = 0; a < 9 && !e; ++a)
+        if (!s->row_va[a].init(&s->drv, s->device, rows * kRowElem[a], kRowPageRows * kRowElem[a]))
+            e = cudaErrorMemoryAllocation;
     for (DeviceStep* d : {&s->dc, &s->da}) {
         if (!e) e = dmal(&d->inst, kMaxStepItems);
         if (!e) e = dmal(&d->prefix, kMaxStepItems + 1);
@@ -452,8 +580,21 @@ int raster_server_create(const raster_server_config* cfg, raster_server** out) {
         raster_server_destroy(s);
         return e == cudaErrorMemoryAllocation ? RASTER_E_OOM : RASTER_E_CUDA;
     }
-    s->tab_alloc.init((unsigned long long)cfg->table_slots);
-    s->row_alloc.init((unsigned long long)cfg->result_rows);
+    s->tab_arena = reinterpret_cast<Slot*>(s->tab_va.base());
+    s->sig_key = reinterpret_cast<unsigned long long*>(s->row_va[0].base());
+    s->sig_cnt = reinterpret_cast<unsigned int*>(s->row_va[1].base());
+    s->sig_slot = reinterpret_cast<unsigned int*>(s->row_va[2].base());
+    s->parent = reinterpret_cast<int*>(s->row_va[3].base());
+    s->csize = reinterpret_cast<unsigned int*>(s->row_va[4].base());
+    s->cmin = reinterpret_cast<unsigned long long*>(s->row_va[5].base());
+    s->out_key = reinterpret_cast<unsigned long long*>(s->row_va[6].base());
+    s->out_cnt = reinterpret_cast<unsigned int*>(s->row_va[7].base());
+    s->out_cid = reinterpret_cast<unsigned long long*>(s->row_va[8].base());
+    unsigned long long row_cap = kMaxRows;
+    for (int a = 0; a < 9; ++a) row_cap = std::min<unsigned long long>(row_cap, s->row_va[a].bytes() / kRowElem[a]);
+    s->tab_alloc.init(s->tab_va.bytes() / sizeof(Slot));
+    s->row_alloc.init(row_cap);
+    s->row_capacity = (long long)row_cap;
     s->g_con = grid_for_kernel((const void*)k_batch_contract<4, true>, 256);
     s->g_sel = grid_for_kernel((const void*)k_batch_select, kScanBlock);
     s->g_agg = grid_for_kernel((const void*)k_batch_hook, kAggBlock);
@@ -479,6 +620,12 @@ int raster_server_submit(raster_server* s, int64_t request_id, double precision,
         return RASTER_E_ARG;
     }
     table_rows_for(n_total, tau, &r->cap, &r->rows);
+    {
+        const TestLimits lim = test_limits();
+        r->max_probe = lim.probe >= 0 ? (unsigned int)std::min<unsigned long long>((unsigned long long)lim.probe, r->cap)
+                                      : (unsigned int)r->cap;
+        if (lim.unions >= 0) r->union_limit = lim.unions;
+    }
     r->t_submit = Clock::now();
     {
         std::unique_lock<std::mutex> lk(s->mu);
@@ -486,7 +633,8 @@ int raster_server_submit(raster_server* s, int64_t request_id, double precision,
             delete r;
             return s->fatal;
         }
-        if (r->cap > s->tab_alloc.capacity() || r->rows > s->row_alloc.capacity()) {
+        if (r->cap > s->tab_alloc.capacity() || r->rows > s->row_alloc.capacity() ||
+            r->cap * sizeof(Slot) + r->rows * kRowBytes + s->reserve > s->total_mem) {
             delete r;
             return RASTER_E_LIMIT;  // could never be admitted
         }
@@ -547,8 +695,8 @@ int raster_server_release(raster_server* s, int64_t request_id) {
     auto it = s->reqs.find(request_id);
     if (it == s->reqs.end() || it->second->state != Request::kDone) return RASTER_E_ARG;
     Request* r = it->second;
-    s->tab_alloc.release(r->tab_off, r->cap);
-    s->row_alloc.release(r->row_off, r->rows);
+    free_table(s, r);
+    free_rows(s, r);
     s->reqs.erase(it);
     delete r;
     lk.unlock();
@@ -566,6 +714,8 @@ int raster_server_stats(raster_server* s, raster_server_stats_t* out) {
     out->completed_unpolled = (int64_t)s->completed.size();
     out->table_slots_used = (int64_t)s->tab_alloc.used();
     out->result_rows_used = (int64_t)s->row_alloc.used();
+    out->device_bytes = (int64_t)mapped_bytes(s);
+    out->refused = s->refused;
     return s->fatal;
 }
 

@@ -58,11 +58,14 @@ constexpr int kUnionLimit = 1 << 30;
 // Host side
 
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<int> g_probe_limit{-1};
+std::atomic<int> g_union_limit{-1};
 
 }  // namespace
 
 namespace raster {
 void note_launch(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+TestLimits test_limits() { return TestLimits{g_probe_limit.load(), g_union_limit.load()}; }
 }  // namespace raster
 
 namespace {
@@ -86,6 +89,9 @@ struct raster_handle {
     bool general = false;
     bool groups = false;  // the 2 x 2 group rule of Sect. 3.6
     int dims = 2;         // coordinates per point: 2 or 3
+    int probe_limit = -1;  // test bound of an insertion's probes (negative: the library's own)
+    unsigned long long* d_sum = nullptr;  // scratch of raster_contract_tiles
+    int union_limit = kUnionLimit;
     bool round_grew = false;  // the table was grown at the start of the current round
     // device copy of the points of raster_cluster_host (kept for the labels)
     double* res_xy = nullptr;
@@ -207,6 +213,13 @@ unsigned int max_probe_for(unsigned long long cap) {
     return (unsigned int)std::min<unsigned long long>(cap, kBucketSlots);  // probing wraps within a bucket
 }
 
+// The probe bound of an insertion: `bound`, or a test's lower one.  Lookups
+// always take the full bound, so a lowered limit can only make insertions
+// fail (RASTER_E_TABLE_FULL), never hide a tile.
+unsigned int insert_probe(const raster_handle* h, unsigned int bound) {
+    return h->probe_limit >= 0 ? std::min<unsigned int>(bound, (unsigned int)h->probe_limit) : bound;
+}
+
 RegionTable table_of(const raster_handle* h) {
     RegionTable t;
     t.tab = h->tab;
@@ -271,7 +284,7 @@ int grow_table(raster_handle* h, unsigned int regions, unsigned int bits) {
     t.regions = regions;
     t.region_bits = bits;
     t.dims = h->dims;
-    t.max_probe = max_probe_for(new_cap);
+    t.max_probe = insert_probe(h, max_probe_for(new_cap));
     if (h->tab && h->cap && !h->fresh) {
         static int grid = grid_for((const void*)k_rehash, kBlock);
         k_rehash<<<grid, kBlock, 0, h->stream>>>(h->tab, h->cap, t, h->d_status);
@@ -457,7 +470,7 @@ int round_finish(raster_handle* h, long long n) {
     if (!by_bucket) {
         static int g2 = grid_for((const void*)k_insert, kBlock);
         RegionTable ti = t;
-        ti.max_probe = std::min<unsigned int>(t.max_probe, kInsertProbe);
+        ti.max_probe = insert_probe(h, std::min<unsigned int>(t.max_probe, kInsertProbe));
         RCHECK(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), h->stream));
         k_insert<<<g2, kBlock, 0, h->stream>>>(ti, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
                                               (unsigned long long)((double)h->cap * kNewLimit), h->d_ctr,
@@ -489,7 +502,8 @@ int round_finish(raster_handle* h, long long n) {
         static int gi = grid_for((const void*)k_insert_bucket, kInsBlock, bsmem);
         k_insert_bucket<<<(int)std::min<unsigned long long>((unsigned long long)gi, n_buckets), kInsBlock, bsmem,
                           h->stream>>>(h->tab, n_buckets, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0,
-                                       (unsigned int)(kNewLimit * kBucketSlots), h->d_ctr, h->d_ctr + 6, h->ovf_key,
+                                       (unsigned int)(kNewLimit * kBucketSlots), insert_probe(h, kBucketProbe),
+                                       h->d_ctr, h->d_ctr + 6, h->ovf_key,
                                        h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
         h->fresh = false;  // every bucket has been written
         note_launch(3);
@@ -511,7 +525,9 @@ int round_finish(raster_handle* h, long long n) {
     }
     if (ovf > 0) {
         static int g3 = grid_for((const void*)k_reinsert, kBlock);
-        k_reinsert<<<g3, kBlock, 0, h->stream>>>(table_of(h), h->ovf_key, h->ovf_cnt, ovf, h->d_ctr, h->d_status);
+        RegionTable tr = table_of(h);
+        tr.max_probe = insert_probe(h, tr.max_probe);
+        k_reinsert<<<g3, kBlock, 0, h->stream>>>(tr, h->ovf_key, h->ovf_cnt, ovf, h->d_ctr, h->d_status);
         note_launch();
         RCHECK(h, cudaGetLastError());
         rc = read_counters(h);
@@ -769,6 +785,11 @@ int raster_create_ex(const raster_params* params, raster_handle** out) {
     h->mu = mu;
     h->groups = params->groups != 0;
     h->dims = dims;
+    {
+        const TestLimits lim = test_limits();
+        h->probe_limit = lim.probe;
+        if (lim.unions >= 0) h->union_limit = lim.unions;
+    }
     if (const char* m = std::getenv("RASTER_LABEL_INDEX")) h->lidx_mode = m[0] == '0' ? -1 : m[0] == '1' ? 1 : 0;
     h->general = dims == 3 || !(params->metric == RASTER_CHEBYSHEV && params->delta == 1);
     {
@@ -829,6 +850,43 @@ int raster_reserve(raster_handle* h, int64_t n_tiles) {
     geometry_for(need, &regions, &bits);
     if (((unsigned long long)regions << bits) > (1ull << 32)) return RASTER_E_OOM;
     return grow_table(h, regions, bits);
+}
+
+int raster_contract_tiles(raster_handle* h, const int64_t* key, const uint32_t* count, int64_t n, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!key || !count || ((uintptr_t)key & 7u) || ((uintptr_t)count & 3u))))
+        return RASTER_E_ARG;
+    if (hard_error(h->status)) return h->status;
+    h->stream = (cudaStream_t)stream;
+    if (n == 0) return RASTER_OK;
+    // the points these tiles stand for, against the 32-bit count limit
+    if (!h->d_sum) RCHECK(h, cudaMalloc(&h->d_sum, sizeof(unsigned long long)));
+    RCHECK(h, cudaMemsetAsync(h->d_sum, 0, sizeof(unsigned long long), h->stream));
+    const int gs = (int)std::min<long long>(1024, (n + kBlock - 1) / kBlock);
+    k_sum_counts<<<gs, kBlock, 0, h->stream>>>(count, n, h->d_sum);
+    note_launch();
+    unsigned long long points = 0;
+    RCHECK(h, cudaMemcpyAsync(&points, h->d_sum, sizeof(points), cudaMemcpyDeviceToHost, h->stream));
+    RCHECK(h, cudaStreamSynchronize(h->stream));
+    if ((unsigned long long)h->points + points > 0xFFFFFFFFull) return RASTER_E_ARG;
+    // room for every key as a new tile at the growth load, then one pass of inserts
+    int rc = raster_reserve(h, (int64_t)std::min<unsigned long long>((unsigned long long)h->d_bound + (unsigned long long)n,
+                                                                     0x7FFFFFFFull));
+    if (rc) return rc;
+    rc = ensure_clean(h);
+    if (rc) return rc;
+    h->state = raster_handle::kContracting;
+    h->points += (long long)points;
+    RegionTable t = table_of(h);
+    t.max_probe = insert_probe(h, t.max_probe);
+    static int g_add = grid_for((const void*)k_add_tiles, kBlock);
+    k_add_tiles<<<(int)std::min<long long>(g_add, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
+        t, reinterpret_cast<const unsigned long long*>(key), count, n, h->d_ctr, h->d_status);
+    note_launch();
+    RCHECK(h, cudaGetLastError());
+    rc = read_counters(h);
+    if (rc) return rc;
+    h->d_bound = (long long)h->h_ctr[0];
+    return RASTER_OK;
 }
 
 int raster_contract(raster_handle* h, const double* xy, int64_t n, void* stream) {
@@ -923,11 +981,12 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     if (h->general)
         k_hook<true><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->d_nbr,
                                                                            h->nbr.n, h->dims, h->parent,
-                                                                           h->d_work + 1, h->d_status);
+                                                                           h->union_limit, h->d_work + 1,
+                                                                           h->d_status);
     else
         k_hook<false><<<std::min<long long>(g_hook, F * lim), kBlock, 0, s>>>(d_nsig, h->sig_key, table_of(h), h->d_nbr,
-                                                                            4, 2, h->parent, h->d_work + 1,
-                                                                            h->d_status);
+                                                                            4, 2, h->parent, h->union_limit,
+                                                                            h->d_work + 1, h->d_status);
     const unsigned long long order_xor = h->dims == 3 ? kOrderXor3 : kOrderXor2;
     k_flatten_stats<<<std::min(g_flat, lim), kBlock, 0, s>>>(d_nsig, h->parent, h->sig_key, h->csize, h->cmin,
                                                              h->d_work + 2, order_xor);
@@ -1219,6 +1278,12 @@ int64_t raster_table_capacity(const raster_handle* h) { return h ? (int64_t)h->c
 
 uint64_t raster_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int raster_set_test_limits(int32_t probe_limit, int32_t union_limit) {
+    g_probe_limit.store(probe_limit < 0 ? -1 : probe_limit);
+    g_union_limit.store(union_limit < 0 ? -1 : union_limit);
+    return RASTER_OK;
+}
+
 int raster_destroy(raster_handle* h) {
     if (!h) return RASTER_E_ARG;
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -1226,7 +1291,7 @@ int raster_destroy(raster_handle* h) {
                     h->csize,  h->cmin,    h->out_key,  h->out_cnt, h->out_cid, h->stage_xy[0], h->stage_xy[1],
                     h->stage_lab[0], h->stage_lab[1], h->stage_keys, h->cursor, h->item_start, h->ovf_key,
                     h->ovf_cnt, h->d_work, h->out_slot, h->point_rr, h->row_count, h->scan_sums,
-                    h->stage2,  h->bcursor, h->d_nbr, h->res_xy, h->lidx, h->lbitmap, h->d_lidx};
+                    h->stage2,  h->bcursor, h->d_nbr, h->res_xy, h->lidx, h->lbitmap, h->d_lidx, h->d_sum};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);

@@ -140,7 +140,7 @@ template <bool GENERAL>
 __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
                                                 const unsigned long long* __restrict__ sig_key, RegionTable t,
                                                 const NbrSet* __restrict__ nbr, int nfwd, int dims, int* parent,
-                                                unsigned long long* work, unsigned int* d_status) {
+                                                int union_limit, unsigned long long* work, unsigned int* d_status) {
     __shared__ long long s_chunk;
     const long long S = (long long)*d_nsig;
     unsigned int st = 0;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsi
                 const unsigned long long nk = pack_key((int)nx, (int)ny);
                 const Slot nb = rt_get(t, nk);
                 if (nb.key != nk || nb.aux == kAuxNone) continue;
-                if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
+                if (!uf_unite(parent, (int)i, (int)nb.aux, union_limit)) st |= kStInternal;
             }
         }
         if (st) atomicOr(d_status, st);
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsi
         }
         const Slot nb = rt_get(t, nk);
         if (nb.key != nk || nb.aux == kAuxNone) continue;
-        if (!uf_unite(parent, (int)i, (int)nb.aux, kUnionLimit)) st |= kStInternal;
+        if (!uf_unite(parent, (int)i, (int)nb.aux, union_limit)) st |= kStInternal;
     }
     if (st) atomicOr(d_status, st);
 }

@@ -321,9 +321,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
 // false when the key finds neither itself nor an empty slot within
 // kBucketProbe slots (the bucket is nearly full).
 constexpr unsigned int kBucketProbe = 128;
-__device__ __forceinline__ bool bucket_add(Slot* s_tab, unsigned long long key) {
+__device__ __forceinline__ bool bucket_add(Slot* s_tab, unsigned long long key, unsigned int max_probe) {
     unsigned int i = tile_hash(key) & (kBucketSlots - 1u);
-    for (unsigned int p = 0; p < kBucketProbe; ++p) {
+    for (unsigned int p = 0; p < max_probe; ++p) {
         unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s_tab[i].key);
         if (k == kEmptyKey) k = atomicCAS(&s_tab[i].key, kEmptyKey, key);
         if (k == kEmptyKey || k == key) {
@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ 
                                                             const unsigned long long* __restrict__ stage2,
                                                             unsigned long long seg2,
                                                             const unsigned int* __restrict__ bcursor, int fresh,
-                                                            unsigned int limit, unsigned long long* d_newkeys,
+                                                            unsigned int limit, unsigned int max_probe,
+                                                            unsigned long long* d_newkeys,
                                                             unsigned long long* d_full, unsigned long long* ovf_key,
                                                             unsigned int* ovf_cnt, unsigned long long* ovf_n,
                                                             unsigned long long* work) {
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ 
             for (int u = 0; u < kInsertUnroll; ++u) {
                 bool spill = false;
                 if (kk[u] != kInvalidKey) {
-                    if (*reinterpret_cast<volatile int*>(&s_full) || !bucket_add(s_tab, kk[u])) {
+                    if (*reinterpret_cast<volatile int*>(&s_full) || !bucket_add(s_tab, kk[u], max_probe)) {
                         spill = true;
                         s_full = 1;
                         ++full;
@@ -509,6 +510,54 @@ __global__ void k_reinsert(RegionTable t, const unsigned long long* __restrict__
     unsigned int newk = 0, st = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int rc = rt_add(t, ovf_key[i], ovf_cnt[i]);
+        if (rc > 0)
+            ++newk;
+        else if (rc < 0)
+            st |= kStFull;
+    }
+    if (newk) atomicAdd(d_newkeys, (unsigned long long)newk);
+    if (st) atomicOr(d_status, st);
+}
+
+// Tiles counted elsewhere, added to the table: count[i] points of tile key[i]
+// (the join of partial count maps, as when P-RASTER joins its per-thread maps,
+// Sect. 3.5).  Keys outside the valid index range are skipped and reported.
+__global__ void k_sum_counts(const unsigned int* __restrict__ count, long long n, unsigned long long* sum) {
+    unsigned long long s = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += count[i];
+    __syncwarp();
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(sum, s);
+}
+
+__device__ __forceinline__ bool valid_tile_key(unsigned long long k, int dims) {
+    if (dims == 3) {
+        if (k >> 63) return false;
+        for (int a = 0; a < 3; ++a) {
+            const int v = key3(k, a);
+            if (v < kMin3 || v > kMax3) return false;
+        }
+        return true;
+    }
+    const int x = key_x(k), y = key_y(k);
+    return x != INT_MIN && x != INT_MAX && y != INT_MIN && y != INT_MAX;
+}
+
+__global__ void k_add_tiles(RegionTable t, const unsigned long long* __restrict__ key,
+                            const unsigned int* __restrict__ count, long long n, unsigned long long* d_newkeys,
+                            unsigned int* d_status) {
+    unsigned int newk = 0, st = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = key[i];
+        const unsigned int c = count[i];
+        if (c == 0) continue;
+        if (!valid_tile_key(k, t.dims)) {
+            st |= kStRange;
+            continue;
+        }
+        const int rc = rt_add(t, k, c);
         if (rc > 0)
             ++newk;
         else if (rc < 0)

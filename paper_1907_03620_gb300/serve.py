@@ -1,6 +1,6 @@
 """Served form: client side of the continuous-batching engine (libraster.so).
 
-    srv = RasterServer(table_slots=1 << 31, result_rows=1 << 28, max_active=4096)
+    srv = RasterServer(max_active=4096, reserve_bytes=4 << 30)
     srv.submit(rid, precision, tau, mu, n_total, n_chunks)
     srv.push(rid, chunk_xy)            # CUDA (n, 2) float64; kept alive until done
     rid, res, latency_ms = srv.poll()  # a completed request (Result), or None
@@ -21,10 +21,14 @@ from ._native import check, lib
 
 
 class RasterServer:
-    def __init__(self, table_slots: int = 1 << 30, result_rows: int = 1 << 26, max_active: int = 4096):
+    def __init__(self, max_active: int = 4096, reserve_bytes: int = 1 << 30, table_slots: int = 0,
+                 result_rows: int = 0):
+        """Requests are admitted while free device memory, less reserve_bytes,
+        covers their tables and rows; table_slots and result_rows optionally
+        bound what the engine holds at once (0: no bound beyond the device)."""
         self._L = lib()
         h = ctypes.c_void_p()
-        cfg = _native.ServerConfig(int(table_slots), int(result_rows), int(max_active))
+        cfg = _native.ServerConfig(int(table_slots), int(result_rows), int(max_active), int(reserve_bytes))
         check(self._L.raster_server_create(ctypes.byref(cfg), ctypes.byref(h)), "raster_server_create")
         self._h = h
         self._alive: dict[int, list] = {}
@@ -49,7 +53,7 @@ class RasterServer:
                                         ctypes.byref(lat))
         if st == _native.E_STATE:
             return None
-        if st not in (_native.OK, _native.E_RANGE, _native.E_TABLE_FULL, _native.E_INTERNAL):
+        if st not in (_native.OK, _native.E_RANGE, _native.E_TABLE_FULL, _native.E_INTERNAL, _native.E_OOM):
             raise _native.RasterError(st, "raster_server_poll")
         n = out.n_tiles
         key = _view(out.key, n, torch.int64, self.device)

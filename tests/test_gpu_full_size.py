@@ -1,8 +1,14 @@
 """The 500M-point workload in the bench's launch configuration (one handle,
-the whole array in one contract call), checked where the oracle can follow
-it: sampled tile counts are recomputed one by one over all points, sampled
-clusters are re-grown from the exported counts, sampled labels are checked,
-and the totals must hold."""
+the whole array in one contract call), bit for bit against the oracle: every
+tile's (key, count), every kept tile's (key, count, cluster id) and all 500M
+labels are hashed the same way as the oracle's stored outputs
+(tests/golden/digests.py); a mismatch names the block of rows and recounts
+its first tiles with the oracle.  Sampled tile counts are also recomputed one
+by one over all points, sampled clusters are re-grown from the exported
+counts, sampled labels are checked, and the totals must hold."""
+import os
+import sys
+
 import numpy as np
 import pytest
 import torch
@@ -13,6 +19,9 @@ import paper_1907_03620_gb300 as R
 
 pytestmark = pytest.mark.gpu
 
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import digests  # noqa: E402
+
 
 def _sorted_lookup(sorted_keys, values, q):
     i = np.searchsorted(sorted_keys, q)
@@ -21,7 +30,30 @@ def _sorted_lookup(sorted_keys, values, q):
     return found, np.where(found, values[i], 0)
 
 
-def test_workload_500m_sampled():
+def _check_digests(xy, w, res, tk, tc, lab):
+    g = digests.load("500m")
+    assert g["workload"] == w.asdict()
+    assert (len(tk), res.n_significant, res.n_clusters, len(res.key)) == \
+        (g["n_tiles"], g["n_significant"], g["n_clusters"], g["n_kept"])
+    rows = digests.canonical_rows(tk, tc)
+    b = digests.first_mismatch(digests.block_digests(rows), g["tiles_blocks"])
+    if b >= 0:
+        lo = len(rows[0]) * b // digests.BLOCKS
+        keys = rows[0][lo:lo + 10_000]
+        want = oracle.count_keys(xy, oracle.scale_of(w.precision), keys)
+        bad = np.flatnonzero(want != rows[1][lo:lo + 10_000])
+        detail = f"first differing row {lo + bad[0]}: key {keys[bad[0]]}" if len(bad) else "not in its first rows"
+        pytest.fail(f"tile block {b} differs from the oracle's; {detail}")
+    b = digests.first_mismatch(digests.block_digests(digests.canonical_rows(
+        res.key.cpu().numpy(), res.count.cpu().numpy(), res.cid.cpu().numpy())), g["kept_blocks"])
+    assert b < 0, f"kept-tile block {b} of {digests.BLOCKS} differs from the oracle's"
+    lab_h = lab.cpu().numpy()
+    assert int((lab_h == oracle.NOISE).sum()) == g["n_noise_points"]
+    b = digests.first_mismatch(digests.block_digests([lab_h.astype("<i8")]), g["labels_blocks"])
+    assert b < 0, f"labels of points [{w.n * b // 64}, {w.n * (b + 1) // 64}) differ from the oracle's"
+
+
+def test_workload_500m_bit_exact():
     w = gen.C3_500M
     xy = gen.points(w)
     d = torch.from_numpy(xy).cuda()
@@ -32,6 +64,7 @@ def test_workload_500m_sampled():
     lab = r.point_labels(d)
     tk, tc = tk.cpu().numpy(), tc.cpu().numpy()
     assert len(tk) == res.n_distinct and int(tc.sum()) == w.n
+    _check_digests(xy, w, res, tk, tc, lab)
     assert res.n_significant == int((tc >= w.tau).sum())
     order = np.argsort(tk)
     sk, sc = tk[order], tc[order]

@@ -146,3 +146,43 @@ def test_zero_point_request():
     got = _drain(srv, 1)
     assert got[1][0].key.numel() == 0 and got[1][0].n_clusters == 0
     srv.close()
+
+
+def test_served_mix_bit_exact_against_stored_oracle():
+    """A mix spanning the served workload's range -- sizes 1e4..2e7, 1..8
+    chunks, every (p, tau, mu) combination -- submitted at once with chunks
+    pushed round-robin: every request's rows hash to the oracle's stored
+    digest (tests/golden/digests.py); a differing request is re-run through
+    the oracle to show the first wrong row."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import digests
+    g = digests.load("served_mix")
+    mix = digests.served_mix(g["seed"])
+    assert len(mix) == len(g["requests"]) == 36
+    dev = {j: torch.from_numpy(gen.points(w)).cuda() for j, (w, c) in enumerate(mix)}
+    srv = RasterServer(max_active=64)
+    for j, (w, c) in enumerate(mix):
+        srv.submit(j, w.precision, w.tau, w.mu, w.n, c)
+    pending = {j: list(gen.chunk_bounds(w.n, c)) for j, (w, c) in enumerate(mix)}
+    while pending:
+        for j in list(pending):
+            lo, hi = pending[j].pop(0)
+            srv.push(j, dev[j][lo:hi])
+            if not pending[j]:
+                del pending[j]
+    got = _drain(srv, len(mix), timeout_s=300.0)
+    for j, (w, c) in enumerate(mix):
+        res, want = got[j][0], g["requests"][j]
+        assert (w.n, c, w.precision, w.tau, w.mu) == (want["n"], want["chunks"], want["precision"], want["tau"],
+                                                      want["mu"])
+        assert res.status == 0
+        stats = (res.n_distinct, res.n_significant, res.n_clusters, res.key.numel())
+        assert stats == (want["n_tiles"], want["n_significant"], want["n_clusters"], want["n_kept"]), j
+        h = digests.rows_digest(res.key.cpu().numpy(), res.count.cpu().numpy(), res.cid.cpu().numpy())
+        if h != want["rows"]:
+            ref, _ = oracle.raster(dev[j].cpu().numpy(), w.precision, w.tau, w.mu)
+            _same(res, ref)
+            pytest.fail(f"request {j} differs from the stored oracle digest")
+    srv.close()
