@@ -400,9 +400,9 @@ def served_leg(args, dev):
 
     th = threading.Thread(target=poller, daemon=True)
     th.start()
-    for k in range(min(pool_n, 64)):  # warm-up
+    for k in range(pool_n):  # warm-up: every request once (the engine maps its pages on first use)
         submit(10**9 + k, k)
-    wait_done(min(pool_n, 64))
+    wait_done(pool_n)
     take()
     # saturation: the whole pool submitted at once
     t0 = time.perf_counter()

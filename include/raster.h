@@ -142,6 +142,22 @@ int raster_reserve(raster_handle *h, int64_t n_tiles);
  * must stay below 2^32. */
 int raster_contract(raster_handle *h, const double *xy, int64_t n, void *stream);
 
+/* Add tiles counted elsewhere: count[i] points to tile key[i], as if those
+ * points had been contracted into this handle.  This is the join of partial
+ * count maps that P-RASTER performs after its parallel contraction (Sect.
+ * 3.5), and the step a sharded run uses when the tiles of a vertical slice
+ * arrive at the device that owns it (Alg. 2).
+ * key: DEVICE int64 tile keys (8-byte aligned) in the handle's packing (two
+ *   int32 indices, or three 21-bit fields for dims = 3); count: DEVICE uint32
+ *   (4-byte aligned); both caller-owned, n >= 0 entries; a key may repeat.
+ * A key outside the valid index range is skipped (RASTER_E_RANGE, reported
+ * like a range error of contraction); counts of 0 are ignored.  Grows the
+ * table first so every key fits, and synchronises `stream` twice (to read
+ * the points the counts stand for, and the table's tile count).
+ * RASTER_E_ARG for bad pointers or if the handle's total points would reach
+ * 2^32. */
+int raster_contract_tiles(raster_handle *h, const int64_t *key, const uint32_t *count, int64_t n, void *stream);
+
 /* Contraction of one chunk (Alg. 1 first loop; Sect. 3.6) as raster_contract,
  * but xy is in HOST memory (pinned for full speed).  The
  * points are streamed through device staging buffers, copies overlapping the

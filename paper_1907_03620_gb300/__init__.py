@@ -163,6 +163,16 @@ class Raster:
         check(self._L.raster_contract(self._h, ctypes.c_void_p(xy.data_ptr()), xy.shape[0], _stream_ptr(stream)),
               "raster_contract")
 
+    def contract_tiles(self, key: torch.Tensor, count: torch.Tensor, stream=None):
+        """Add count[i] points to tile key[i] (CUDA int64 keys, CUDA int32 or
+        uint32-valued counts): the join of partial tile counts."""
+        assert key.is_cuda and key.dtype == torch.int64 and key.is_contiguous()
+        assert count.is_cuda and count.dtype == torch.int32 and count.is_contiguous()
+        assert key.numel() == count.numel()
+        check(self._L.raster_contract_tiles(self._h, ctypes.c_void_p(key.data_ptr()),
+                                            ctypes.c_void_p(count.data_ptr()), key.numel(), _stream_ptr(stream)),
+              "raster_contract_tiles")
+
     def contract_host(self, xy, stream=None):
         """xy: host (n, 2) float64 (pinned torch tensor or numpy array)."""
         ptr, n = _host_ptr(xy, cols=self.dims)

@@ -94,6 +94,7 @@ def _declare(L):
         "raster_contract": (ci, [vp, vp, i64, vp]),
         "raster_contract_host": (ci, [vp, vp, i64, vp]),
         "raster_agglomerate": (ci, [vp, ctypes.POINTER(Clusters)]),
+        "raster_contract_tiles": (ci, [vp, vp, vp, i64, vp]),
         "raster_point_labels": (ci, [vp, vp, i64, vp, vp]),
         "raster_point_labels_host": (ci, [vp, vp, i64, vp, vp]),
         "raster_cluster_host": (ci, [vp, vp, i64, vp, ctypes.POINTER(Clusters), vp]),

@@ -496,15 +496,18 @@ int round_finish(raster_handle* h, long long n) {
         const size_t bsmem = sizeof(Slot) * kBucketSlots;
         static bool battr = false;
         if (!battr) {
-            RCHECK(h, cudaFuncSetAttribute(k_insert_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+            RCHECK(h, cudaFuncSetAttribute(k_insert_bucket<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bsmem));
+            RCHECK(h, cudaFuncSetAttribute(k_insert_bucket<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bsmem));
             battr = true;
         }
-        static int gi = grid_for((const void*)k_insert_bucket, kInsBlock, bsmem);
-        k_insert_bucket<<<(int)std::min<unsigned long long>((unsigned long long)gi, n_buckets), kInsBlock, bsmem,
-                          h->stream>>>(h->tab, n_buckets, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0,
-                                       (unsigned int)(kNewLimit * kBucketSlots), insert_probe(h, kBucketProbe),
-                                       h->d_ctr, h->d_ctr + 6, h->ovf_key,
-                                       h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
+        static int gi = grid_for((const void*)k_insert_bucket<false>, kInsBlock, bsmem);
+        const unsigned int probe = insert_probe(h, kBucketProbe);
+        auto ins = probe < kBucketProbe ? k_insert_bucket<true> : k_insert_bucket<false>;
+        ins<<<(int)std::min<unsigned long long>((unsigned long long)gi, n_buckets), kInsBlock, bsmem, h->stream>>>(
+            h->tab, n_buckets, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0, (unsigned int)(kNewLimit * kBucketSlots),
+            probe, h->d_ctr, h->d_ctr + 6, h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
         h->fresh = false;  // every bucket has been written
         note_launch(3);
         RCHECK(h, cudaGetLastError());

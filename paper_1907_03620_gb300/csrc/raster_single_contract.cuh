@@ -321,9 +321,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
 // false when the key finds neither itself nor an empty slot within
 // kBucketProbe slots (the bucket is nearly full).
 constexpr unsigned int kBucketProbe = 128;
+template <bool LIMITED>
 __device__ __forceinline__ bool bucket_add(Slot* s_tab, unsigned long long key, unsigned int max_probe) {
     unsigned int i = tile_hash(key) & (kBucketSlots - 1u);
-    for (unsigned int p = 0; p < max_probe; ++p) {
+    for (unsigned int p = 0; p < (LIMITED ? max_probe : kBucketProbe); ++p) {
         unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s_tab[i].key);
         if (k == kEmptyKey) k = atomicCAS(&s_tab[i].key, kEmptyKey, key);
         if (k == kEmptyKey || k == key) {
@@ -341,11 +342,13 @@ __device__ __forceinline__ bool bucket_add(Slot* s_tab, unsigned long long key, 
 // shared-memory atomics, and the bucket is written back whole.  New tiles are
 // counted once per bucket, as the growth of its occupied slots.  A key that
 // finds no room within kBucketProbe slots goes to the overflow list and
-// switches the bucket to passing its remaining keys there unprobed; such keys,
+// switches the bucket to passing its remaining keys there unprobed (LIMITED:
+// a test's lower probe bound, max_probe, in place of kBucketProbe); such keys,
 // and a bucket left holding more than `limit` tiles, are counted in *d_full so
 // that the host grows the table.
 constexpr int kInsBlock = 512;
 constexpr int kInsertUnroll = 4;
+template <bool LIMITED>
 __global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ tab, unsigned long long n_buckets,
                                                             const unsigned long long* __restrict__ stage2,
                                                             unsigned long long seg2,
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ 
             for (int u = 0; u < kInsertUnroll; ++u) {
                 bool spill = false;
                 if (kk[u] != kInvalidKey) {
-                    if (*reinterpret_cast<volatile int*>(&s_full) || !bucket_add(s_tab, kk[u], max_probe)) {
+                    if (*reinterpret_cast<volatile int*>(&s_full) || !bucket_add<LIMITED>(s_tab, kk[u], max_probe)) {
                         spill = true;
                         s_full = 1;
                         ++full;
