@@ -39,11 +39,15 @@ TILE_BYTES = 12          # algorithmic bytes per distinct tile (key + count writ
 POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 
 # DRAM bytes (read + write) of one contraction phase (k_part, k_region_items,
-# k_bucket and k_insert_bucket) in a steady-state step of the 500M-point
-# workload, from one ncu capture with one pass per launch.  Valid only for the
-# kernel sources it was measured with (their digest below); reported as null
-# otherwise.
-MEASURED_CONTRACT_TRAFFIC = {"sources": "290bc7ec24a37d8c", "workload": "raster-500m", "bytes": 31_499_000_000}
+# k_bucket and k_insert_bucket) in a steady-state step, from one ncu capture
+# with one pass per launch on the 100M-point case of the same workload
+# (`--points 100000000`: 1.6 GB of points, a 91M-slot table).  The traffic
+# grows with the points (16 B read, keys staged twice) and with the table
+# slots (each written once), so it scales to a full launch as
+# per_point * n + per_slot * slots.  Valid only for the kernel sources it was
+# measured with (their digest); reported as null otherwise.
+MEASURED_CONTRACT_TRAFFIC = {"sources": "4fc09f4e6912edf7", "case_points": 100_000_000, "case_slots": 91_226_112,
+                             "per_point": 4.749e9 / 100_000_000, "per_slot": 1.394e9 / 91_226_112}
 
 
 def kernel_sources_digest() -> str:
@@ -537,13 +541,14 @@ def run_gpu(args):
     alg_bytes = POINT_BYTES * w.n + TILE_BYTES * res.n_distinct
     achieved = alg_bytes / (contract_ms / 1e3) / 1e9
     traffic = None
-    if (not args.points and args.workload == "500m"
-            and kernel_sources_digest() == MEASURED_CONTRACT_TRAFFIC["sources"]):
-        traffic = MEASURED_CONTRACT_TRAFFIC["bytes"]
+    if kernel_sources_digest() == MEASURED_CONTRACT_TRAFFIC["sources"]:
+        traffic = round(MEASURED_CONTRACT_TRAFFIC["per_point"] * w.n + MEASURED_CONTRACT_TRAFFIC["per_slot"] * r.capacity)
     roofline = {"bound": "hbm", "kernel": "contraction phase: k_part + k_region_items + k_bucket + k_insert_bucket",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"] + " (copy bandwidth)",
-                "traffic": traffic, "traffic_unit": "bytes per contraction phase (ncu dram__bytes read+write)",
+                "traffic": traffic,
+                "traffic_unit": ("bytes per contraction phase (ncu dram__bytes read+write on the 100M-point case, "
+                                 "scaled per point and per table slot)"),
                 "algorithmic_bytes": alg_bytes, "algorithmic": "16 B/point + 12 B/distinct tile",
                 "phase_ms": contract_ms}
     # the other phases of the step, against the same peak

@@ -395,6 +395,7 @@ constexpr unsigned int kInsertProbe = 1024;      // global insert: longer probe 
 constexpr double kBucketRound = 0.25;            // rounds of fewer points per table slot insert globally
 constexpr double kRefitRatio = 1.5;              // a grown table this much larger than needed is rebuilt
 constexpr double kPreGrow = 4.0;                 // grow before a round whose estimate is this far past kMaxLoad
+constexpr bool kLabelsQueued = true;             // labels with the block index: k_labels_idx (queued fallbacks)
 
 // One contraction round of n points: pass 1, item prefix, pass 1b, pass 2
 // (all asynchronous), then one synchronisation to read the table's tile count
@@ -681,6 +682,13 @@ void launch_labels(raster_handle* h, const double* xy, long long n, int64_t* lab
     LabelIndex li{nullptr, 0, 0, nullptr};
     if (DIMS == 2 && h->lidx_on)
         li = LabelIndex{h->lidx, h->lidx_buckets, h->lidx_share, reinterpret_cast<unsigned int*>(h->d_lidx + 1)};
+    if (DIMS == 2 && h->lidx_on && kLabelsQueued) {
+        static int gq = grid_for((const void*)k_labels_idx<WIDE>, kBlock);
+        k_labels_idx<WIDE><<<(int)std::min<long long>(gq, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
+            xy, n, h->pp, table_of(h), reinterpret_cast<const long long*>(h->out_cid),
+            reinterpret_cast<long long*>(labels), h->d_status, li);
+        return;
+    }
     k_labels<WIDE, DIMS><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
         xy, n, h->pp, table_of(h), h->tau, reinterpret_cast<const long long*>(h->out_cid),
         reinterpret_cast<long long*>(labels), h->d_status, li);

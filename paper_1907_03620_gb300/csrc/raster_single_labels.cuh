@@ -222,6 +222,103 @@ __global__ void k_labels(const double* __restrict__ xy, long long n, ProjParams 
     if (st) atomicOr(d_status, st);
 }
 
+// Labels of two-coordinate points with the block index, without idle lanes.
+// Most points are answered by the first bucket of their block's probe (the
+// block's entry, or an empty second entry: no kept tile there).  The others
+// -- a block that sits in a later bucket, a block whose kept tiles name
+// several cluster ids, a block out of the index's range -- are queued per
+// warp in shared memory and answered 32 at a time, the full index lookup
+// and the table behind it, with every lane busy.  Answering them where they
+// arise left most lanes of a warp idle while a few probed on.
+constexpr int kLabQueue = 64;  // per warp: up to 31 waiting plus 32 new
+
+// 1 with *lab set when the home bucket answers; 0 when the full lookup must.
+__device__ __forceinline__ int lidx_first(const LabelIndex& li, const RegionTable& t, unsigned long long key,
+                                          long long* lab) {
+    unsigned long long bk;
+    if (!lidx_block(key, &bk)) return 0;
+    const ulonglong4 v = lidx_load(li.ent + 4 * lidx_home(key, bk, t, li.share));
+    unsigned long long w, w1;
+    if ((v.x >> 16) == bk) {
+        w = v.x;
+        w1 = v.y;
+    } else if ((v.z >> 16) == bk) {
+        w = v.z;
+        w1 = v.w;
+    } else {
+        if (v.z != 0ull) return 0;  // the block may sit in a later bucket
+        *lab = (long long)kEmptyKey;
+        return 1;
+    }
+    if (!((w1 >> lidx_bit(key)) & 1ull)) {
+        *lab = (long long)kEmptyKey;
+        return 1;
+    }
+    const unsigned int code = (unsigned int)(w & 0xFFFFull);
+    if (code == kLidxMixed) return 0;
+    *lab = (long long)pack_key((key_x(key) & ~7) + (int)(signed char)(code >> 8),
+                               (key_y(key) & ~7) + (int)(signed char)(code & 0xFFu));
+    return 1;
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kBlock) k_labels_idx(const double* __restrict__ xy, long long n, ProjParams pp,
+                                                      RegionTable t, const long long* __restrict__ cid_rows,
+                                                      long long* __restrict__ labels, unsigned int* d_status,
+                                                      LabelIndex li) {
+    __shared__ unsigned long long s_key[kBlock / 32][kLabQueue];
+    __shared__ long long s_idx[kBlock / 32][kLabQueue];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool index_ok = *li.bad == 0u;
+    const long long warps_total = (long long)gridDim.x * (kBlock / 32);
+    unsigned int st = 0;
+    int qn = 0;  // warp-uniform
+    // the last `count` queued points, one per lane
+    auto drain = [&](int count) {
+        if (lane < count) {
+            const unsigned long long key = s_key[warp][qn - count + lane];
+            const long long i = s_idx[warp][qn - count + lane];
+            long long lab = (long long)kEmptyKey;
+            if (!(index_ok && lidx_label(li, t, key, &lab))) {
+                const Slot sl = rt_get(t, key);
+                if (sl.key == key) lab = label_decode(key, sl.aux, cid_rows);  // kAuxNone decodes to noise
+            }
+            __stcs(labels + i, lab);
+        }
+        qn -= count;
+        __syncwarp();
+    };
+    for (long long base = ((long long)blockIdx.x * (kBlock / 32) + warp) * 32; base < n; base += warps_total * 32) {
+        const long long i = base + lane;
+        unsigned long long key = kInvalidKey;
+        long long lab = (long long)kEmptyKey;
+        bool defer = false, have = false;
+        if (i < n) {
+            key = project_in<WIDE, 2>(load_point<2>(xy, i), pp);
+            if (key == kInvalidKey) {
+                st |= kStRange;
+                have = true;
+            } else if (index_ok && lidx_first(li, t, key, &lab)) {
+                have = true;
+            } else {
+                defer = true;
+            }
+        }
+        const unsigned int m = __ballot_sync(0xFFFFFFFFu, defer);
+        if (defer) {
+            const int pos = qn + __popc(m & ((1u << lane) - 1u));
+            s_key[warp][pos] = key;
+            s_idx[warp][pos] = i;
+        }
+        qn += __popc(m);
+        __syncwarp();
+        if (have) __stcs(labels + i, lab);
+        if (qn >= 32) drain(32);
+    }
+    if (qn > 0) drain(qn);
+    if (st) atomicOr(d_status, st);
+}
+
 // RASTER' (Sect. 3.4): the points of every kept tile, as a CSR over result
 // rows.  The slots of kept tiles temporarily hold their result row in aux.
 __global__ void k_aux_rows(const unsigned long long* d_nkept, const unsigned int* __restrict__ out_slot, Slot* tab) {
