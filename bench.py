@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=10_000_000, help="points of the oracle sample")
-    ap.add_argument("--cpu-parallel-sample", type=int, default=100_000_000,
+    ap.add_argument("--cpu-parallel-sample", type=int, default=500_000_000,
                     help="points of the multi-threaded P-RASTER sample")
     ap.add_argument("--profile", action="store_true", help="short run for ncu (no clocks/e2e/cpu legs)")
     ap.add_argument("--points", type=int, default=0, help="use only the first N points (profiling cases)")

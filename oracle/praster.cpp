@@ -78,6 +78,71 @@ double now() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Open-addressing hash map from tile key to a 64-bit value (linear probing,
+// at most half full; the unreachable key INT64_MIN marks an empty slot).  A
+// flat table keeps every thread's inserts free of the allocator.
+class FlatMap {
+public:
+    explicit FlatMap(size_t expect = 16) { rehash(capacity_for(expect)); }
+    uint64_t &get(int64_t k) {  // the value of k, inserted as 0 if absent
+        if ((n_ + 1) * 2 > keys_.size()) rehash(keys_.size() * 2);
+        size_t i = home(k);
+        while (keys_[i] != kEmpty && keys_[i] != k) i = (i + 1) & mask_;
+        if (keys_[i] == kEmpty) {
+            keys_[i] = k;
+            vals_[i] = 0;
+            ++n_;
+        }
+        return vals_[i];
+    }
+    const uint64_t *find(int64_t k) const {
+        size_t i = home(k);
+        while (keys_[i] != kEmpty) {
+            if (keys_[i] == k) return &vals_[i];
+            i = (i + 1) & mask_;
+        }
+        return nullptr;
+    }
+    size_t size() const { return n_; }
+    template <typename F>
+    void each(F f) const {
+        for (size_t i = 0; i < keys_.size(); ++i)
+            if (keys_[i] != kEmpty) f(keys_[i], vals_[i]);
+    }
+    void release() {
+        std::vector<int64_t>().swap(keys_);
+        std::vector<uint64_t>().swap(vals_);
+        n_ = 0;
+    }
+
+private:
+    static constexpr int64_t kEmpty = INT64_MIN;
+    static size_t capacity_for(size_t expect) {
+        size_t c = 16;
+        while (c < 2 * expect + 2) c <<= 1;
+        return c;
+    }
+    size_t home(int64_t k) const { return (size_t)(mix(k) >> shift_); }  // high bits: shares use the low ones
+    void rehash(size_t cap) {
+        std::vector<int64_t> ok;
+        std::vector<uint64_t> ov;
+        ok.swap(keys_);
+        ov.swap(vals_);
+        keys_.assign(cap, kEmpty);
+        vals_.assign(cap, 0);
+        mask_ = cap - 1;
+        shift_ = 64;
+        for (size_t c = cap; c > 1; c >>= 1) --shift_;
+        n_ = 0;
+        for (size_t i = 0; i < ok.size(); ++i)
+            if (ok[i] != kEmpty) get(ok[i]) = ov[i];
+    }
+    std::vector<int64_t> keys_;
+    std::vector<uint64_t> vals_;
+    size_t mask_ = 0, n_ = 0;
+    int shift_ = 64;
+};
+
 struct Cluster {
     std::vector<int64_t> tiles;
     bool left = false, right = false;  // touches the slice's left / right border
@@ -93,7 +158,7 @@ struct praster_state {
     int64_t n_tiles, n_significant, n_clusters;
     std::vector<int64_t> key, cid;
     std::vector<uint64_t> count;
-    std::unordered_map<int64_t, int64_t> cid_of;
+    FlatMap cid_of;  // kept tile -> cluster id (as uint64)
     double t_contract, t_agglomerate, t_labels;
 };
 
@@ -119,34 +184,33 @@ int praster_run(praster_state *s, const double *xy, int64_t n) {
     const double t0 = now();
     // 1. per-thread hash maps over unsorted batches; each thread keeps one map
     // per share of the key space, so that the join reads only its own share
-    std::vector<std::vector<std::unordered_map<int64_t, uint64_t>>> local(T);
+    std::vector<std::vector<FlatMap>> local(T);
     std::vector<int> bad(T, 0);
     parallel(T, [&](int t) {
         const int64_t lo = n * t / T, hi = n * (t + 1) / T;
         auto &m = local[t];
-        m.resize(T);
-        for (auto &x : m) x.reserve((size_t)((hi - lo) / (2 * T) + 16));
+        m.assign(T, FlatMap((size_t)((hi - lo) / (2 * T) + 16)));
         for (int64_t i = lo; i < hi; ++i) {
             int64_t k;
             if (!project(xy, i, s->scale, &k)) {
                 bad[t] = 1;
                 continue;
             }
-            m[(int)(mix(k) % (uint64_t)T)][k] += 1;
+            m[(int)(mix(k) % (uint64_t)T)].get(k) += 1;
         }
     });
     // 2. join: thread t joins share t of every thread's maps (the paper's code
     // joined the maps sequentially)
-    std::vector<std::unordered_map<int64_t, uint64_t>> joined(T);
+    std::vector<FlatMap> joined(T);
     parallel(T, [&](int t) {
-        auto &m = joined[t];
         size_t guess = 0;
         for (auto &l : local) guess = std::max(guess, l[t].size());
-        m.reserve(guess + guess / 2 + 16);
+        FlatMap m(guess + guess / 2 + 16);
         for (auto &l : local) {
-            for (const auto &kv : l[t]) m[kv.first] += kv.second;
-            std::unordered_map<int64_t, uint64_t>().swap(l[t]);
+            l[t].each([&](int64_t k, uint64_t v) { m.get(k) += v; });
+            l[t].release();
         }
+        joined[t] = std::move(m);
     });
     local.clear();
     s->status = *std::max_element(bad.begin(), bad.end()) ? 2 : 0;
@@ -158,8 +222,9 @@ int praster_run(praster_state *s, const double *xy, int64_t n) {
     int64_t tiles = 0;
     for (auto &m : joined) tiles += (int64_t)m.size();
     parallel(T, [&](int t) {
-        for (const auto &kv : joined[t])
-            if (kv.second >= s->tau) sig_part[t].push_back(kv.first);
+        joined[t].each([&](int64_t k, uint64_t v) {
+            if (v >= s->tau) sig_part[t].push_back(k);
+        });
     });
     std::vector<int64_t> sig;
     for (auto &p : sig_part) sig.insert(sig.end(), p.begin(), p.end());
@@ -181,15 +246,19 @@ int praster_run(praster_state *s, const double *xy, int64_t n) {
     for (int64_t k : sig) slice[slice_of(k)].push_back(k);
     std::vector<std::vector<Cluster>> kept(N), cand(N);
     parallel(N, [&](int sl) {
-        std::unordered_set<int64_t> rest(slice[sl].begin(), slice[sl].end());
+        // the slice's tiles; value 1 while not yet visited
+        FlatMap rest(slice[sl].size());
+        for (int64_t k : slice[sl]) rest.get(k) = 1;
         const int64_t x0 = lo_x(sl), x1 = hi_x(sl);
-        while (!rest.empty()) {
+        std::vector<int64_t> visit;
+        for (int64_t start : slice[sl]) {
+            uint64_t &st = rest.get(start);
+            if (!st) continue;
+            st = 0;
             Cluster c;
-            std::deque<int64_t> visit{*rest.begin()};
-            rest.erase(rest.begin());
-            while (!visit.empty()) {
-                const int64_t u = visit.front();
-                visit.pop_front();
+            visit.assign(1, start);
+            for (size_t q = 0; q < visit.size(); ++q) {
+                const int64_t u = visit[q];
                 c.tiles.push_back(u);
                 if (sl > 0 && tx(u) == x0) c.left = true;
                 if (sl < N - 1 && tx(u) == x1) c.right = true;
@@ -199,10 +268,11 @@ int praster_run(praster_state *s, const double *xy, int64_t n) {
                         const int64_t nx = (int64_t)tx(u) + dx, ny = (int64_t)ty(u) + dy;
                         if (nx < -2147483647LL || nx > 2147483646LL || ny < -2147483647LL || ny > 2147483646LL)
                             continue;
-                        auto it = rest.find(pack((int32_t)nx, (int32_t)ny));
-                        if (it != rest.end()) {
-                            visit.push_back(*it);
-                            rest.erase(it);
+                        const int64_t nk = pack((int32_t)nx, (int32_t)ny);
+                        const uint64_t *f = rest.find(nk);
+                        if (f && *f) {
+                            rest.get(nk) = 0;
+                            visit.push_back(nk);
                         }
                     }
             }
@@ -299,14 +369,13 @@ int praster_run(praster_state *s, const double *xy, int64_t n) {
     s->key.resize(rows.size());
     s->cid.resize(rows.size());
     s->count.resize(rows.size());
-    s->cid_of.clear();
-    s->cid_of.reserve(rows.size());
+    s->cid_of = FlatMap(rows.size());
     for (size_t r = 0; r < rows.size(); ++r) {
         s->key[r] = rows[r].first;
         s->cid[r] = rows[r].second;
-        s->cid_of[rows[r].first] = rows[r].second;
+        s->cid_of.get(rows[r].first) = (uint64_t)rows[r].second;
         const auto &m = joined[(int)(mix(rows[r].first) % (uint64_t)T)];
-        s->count[r] = m.at(rows[r].first);
+        s->count[r] = *m.find(rows[r].first);
     }
     s->n_clusters = (int64_t)out.size();
     s->t_agglomerate = now() - t1;
@@ -326,8 +395,8 @@ int praster_labels(praster_state *s, const double *xy, int64_t n, int64_t *label
                 bad[t] = 1;
                 continue;
             }
-            auto it = s->cid_of.find(k);
-            labels[i] = it == s->cid_of.end() ? NOISE : it->second;
+            const uint64_t *c = s->cid_of.find(k);
+            labels[i] = c ? (int64_t)*c : NOISE;
         }
     });
     s->t_labels = now() - t0;
