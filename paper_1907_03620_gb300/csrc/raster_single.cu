@@ -976,8 +976,9 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
         k_groups<<<g_grp, kBlock, 0, s>>>(h->tab, table_of(h), h->tau, h->d_work + 6);
         note_launch();
     }
+    RCHECK(h, cudaMemsetAsync(h->d_work + 3, 0, sizeof(unsigned long long), s));
     k_select<<<g_sel, kBlock, 0, s>>>(h->tab, h->cap, h->tau, h->sig_key, h->sig_cnt, h->sig_slot, d_nsig,
-                                      (unsigned long long)h->agg_cap, 1, h->groups ? 1 : 0);
+                                      (unsigned long long)h->agg_cap, 1, h->groups ? 1 : 0, h->d_work + 3);
     k_clamp_rows<<<1, 1, 0, s>>>(d_nsig, (unsigned long long)h->agg_cap, h->d_status);
     note_launch(2);
     RCHECK(h, cudaGetLastError());

@@ -9,17 +9,27 @@
 
 // Compaction of occupied slots with count >= min_count into (key, count, slot)
 // rows.  With min_count = tau this is the significant-tile selection; each
-// selected slot's aux receives its row index.
+// selected slot's aux receives its row index.  With `work`, blocks claim
+// their tiles of slots in order from that counter, so the rows follow slot
+// order (and table regions); without it they take a static grid stride.
 constexpr int kSelItems = 8;
 __global__ void __launch_bounds__(kBlock) k_select(Slot* tab, unsigned long long cap, unsigned int min_count,
                                                   unsigned long long* out_key, unsigned int* out_cnt,
                                                   unsigned int* out_slot, unsigned long long* d_rows,
-                                                  unsigned long long row_cap, int write_aux, int marked) {
+                                                  unsigned long long row_cap, int write_aux, int marked,
+                                                  unsigned long long* work = nullptr) {
     __shared__ unsigned int scratch[33];
-    __shared__ unsigned long long s_base;
+    __shared__ unsigned long long s_base, s_t0;
     const unsigned long long tile = (unsigned long long)kBlock * kSelItems;
-    for (unsigned long long t0 = (unsigned long long)blockIdx.x * tile; t0 < cap;
-         t0 += (unsigned long long)gridDim.x * tile) {
+    auto next = [&](unsigned long long prev) {  // the block's next tile of slots (prev = ~0: its first)
+        if (!work) return prev == ~0ull ? (unsigned long long)blockIdx.x * tile : prev + (unsigned long long)gridDim.x * tile;
+        if (threadIdx.x == 0) s_t0 = atomicAdd(work, 1ull) * tile;
+        __syncthreads();
+        const unsigned long long v = s_t0;
+        __syncthreads();
+        return v;
+    };
+    for (unsigned long long t0 = next(~0ull); t0 < cap; t0 = next(t0)) {
         unsigned long long k[kSelItems];
         unsigned int c[kSelItems];
         unsigned int flags = 0;
@@ -136,6 +146,9 @@ struct NbrSet {
 // to 40 forward offsets) take one thread per (significant tile, forward
 // neighbour).  Significance is read from the slot: the selection wrote each
 // significant tile's row into aux, every other slot holds kAuxNone.
+constexpr long long kHookStreams = 8;    // chunk streams of the default hook
+constexpr long long kHookSpacing = 256;  // chunks between two streams
+
 template <bool GENERAL>
 __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
                                                 const unsigned long long* __restrict__ sig_key, RegionTable t,
@@ -145,7 +158,17 @@ __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsi
     const long long S = (long long)*d_nsig;
     unsigned int st = 0;
     if (!GENERAL) {
-        for (long long c = next_chunk(work, &s_chunk); c < S; c = next_chunk(work, &s_chunk)) {
+        // Rows come in slot order (the selection claims its slots in order), so
+        // consecutive chunks hold the tiles of the same clusters.  Claims
+        // are spread over kHookStreams streams kHookSpacing chunks apart, so
+        // that the blocks in flight hook into different clusters' roots while
+        // each stream still walks the table in order.
+        const long long G = (long long)kHookStreams * kHookSpacing;
+        const long long nch = (S + kBlock - 1) / kBlock, nclaims = (nch + G - 1) / G * G;
+        for (long long q = next_chunk(work, &s_chunk) / kBlock; q < nclaims; q = next_chunk(work, &s_chunk) / kBlock) {
+            const long long w = q % G;
+            const long long c = ((q - w) + (w % kHookStreams) * kHookSpacing + w / kHookStreams) * kBlock;
+            if (c >= S) continue;  // the last group's claims beyond the rows
             const long long i = c + threadIdx.x;
             if (i >= S) continue;
             const unsigned long long key = sig_key[i];
