@@ -147,7 +147,7 @@ struct NbrSet {
 // neighbour).  Significance is read from the slot: the selection wrote each
 // significant tile's row into aux, every other slot holds kAuxNone.
 constexpr long long kHookStreams = 8;    // chunk streams of the default hook
-constexpr long long kHookSpacing = 256;  // chunks between two streams
+constexpr long long kHookSpacing = 1024;  // chunks between two streams
 
 template <bool GENERAL>
 __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsig,
