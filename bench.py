@@ -373,7 +373,7 @@ def served_leg(args, dev):
 
     def poller():
         while not stop[0]:
-            r = srv.poll(wait_ms=20, copy=False)
+            r = srv.poll(wait_ms=20, rows=False)
             if r is None:
                 continue
             rid, res, lat = r

@@ -396,7 +396,6 @@ constexpr double kBucketRound = 0.25;            // rounds of fewer points per t
 constexpr double kRefitRatio = 1.5;              // a grown table this much larger than needed is rebuilt
 constexpr double kPreGrow = 4.0;                 // grow before a round whose estimate is this far past kMaxLoad
 constexpr bool kLabelsQueued = true;             // labels with the block index: k_labels_idx (queued fallbacks)
-constexpr unsigned int kBucketGroupRegions = 0;  // regions per alternation of passes 1b and 2 (0: all at once)
 
 // One contraction round of n points: pass 1, item prefix, pass 1b, pass 2
 // (all asynchronous), then one synchronisation to read the table's tile count
@@ -504,29 +503,14 @@ int round_finish(raster_handle* h, long long n) {
         static int gi = grid_for((const void*)k_insert_bucket<false>, kInsBlock, bsmem);
         const unsigned int probe = insert_probe(h, kBucketProbe);
         auto ins = probe < kBucketProbe ? k_insert_bucket<true> : k_insert_bucket<false>;
-        // passes 1b and 2 alternate over groups of regions, so that a group's
-        // bucket segments are still in L2 when pass 2 reads them
-        const unsigned int group = kBucketGroupRegions ? kBucketGroupRegions : h->regions;
-        const int bb = (int)h->region_bits - kBucketBits;
-        for (unsigned int r0 = 0; r0 < h->regions; r0 += group) {
-            const unsigned int r1 = std::min(h->regions, r0 + group);
-            const unsigned long long b0 = (unsigned long long)r0 << bb, b1 = (unsigned long long)r1 << bb;
-            if (r0 > 0) {  // the work counters start at the group's first item and bucket
-                RCHECK(h, cudaMemcpyAsync(h->d_work, h->item_start + r0, sizeof(long long), cudaMemcpyDeviceToDevice,
-                                          h->stream));
-                k_set_counter<<<1, 1, 0, h->stream>>>(h->d_work + 1, b0);
-                note_launch();
-            }
-            k_bucket<<<gb, kBlock, kBucketSmem, h->stream>>>(t, h->stage_keys, seg, h->cursor, h->item_start, (int)r1,
-                                                             h->stage2, seg2, h->bcursor, h->ovf_key, h->ovf_cnt,
-                                                             h->d_ctr + 5, h->d_work);
-            ins<<<(int)std::min<unsigned long long>((unsigned long long)gi, b1 - b0), kInsBlock, bsmem, h->stream>>>(
-                h->tab, b1, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0, (unsigned int)(kNewLimit * kBucketSlots),
-                probe, h->d_ctr, h->d_ctr + 6, h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
-            note_launch(2);
-        }
+        k_bucket<<<gb, kBlock, kBucketSmem, h->stream>>>(t, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
+                                                         h->stage2, seg2, h->bcursor, h->ovf_key, h->ovf_cnt,
+                                                         h->d_ctr + 5, h->d_work);
+        ins<<<(int)std::min<unsigned long long>((unsigned long long)gi, n_buckets), kInsBlock, bsmem, h->stream>>>(
+            h->tab, n_buckets, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0, (unsigned int)(kNewLimit * kBucketSlots),
+            probe, h->d_ctr, h->d_ctr + 6, h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
         h->fresh = false;  // every bucket has been written
-        note_launch(1);
+        note_launch(3);
         RCHECK(h, cudaGetLastError());
     }
     rc = read_counters(h);

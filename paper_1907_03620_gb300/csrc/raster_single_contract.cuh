@@ -7,8 +7,6 @@
 // union limits) and the device, region and block helpers.
 #pragma once
 
-__global__ void k_set_counter(unsigned long long* c, unsigned long long v) { *c = v; }
-
 __global__ void k_fill_table(Slot* tab, unsigned long long cap) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     ulonglong2 v;

@@ -45,7 +45,10 @@ class RasterServer:
         check(self._L.raster_server_push(self._h, int(rid), ctypes.c_void_p(xy.data_ptr() if xy.numel() else 0),
                                          xy.shape[0]), "raster_server_push")
 
-    def poll(self, wait_ms: int = 0, copy: bool = True):
+    def poll(self, wait_ms: int = 0, copy: bool = True, rows: bool = True):
+        """A completed request as (id, Result, latency_ms), or None.  rows=False
+        skips building the result tensors (no torch work): the Result then
+        holds the counts and status only, with empty tensors."""
         rid = ctypes.c_int64()
         out = _native.Clusters()
         lat = ctypes.c_double()
@@ -55,6 +58,10 @@ class RasterServer:
             return None
         if st not in (_native.OK, _native.E_RANGE, _native.E_TABLE_FULL, _native.E_INTERNAL, _native.E_OOM):
             raise _native.RasterError(st, "raster_server_poll")
+        if not rows:
+            none = torch.empty(0, dtype=torch.int64)
+            return rid.value, Result(none, none, none, out.n_clusters, out.n_distinct, out.n_significant,
+                                     out.n_points, st), lat.value
         n = out.n_tiles
         key = _view(out.key, n, torch.int64, self.device)
         cnt = _view(out.count, n, torch.int32, self.device)
