@@ -364,6 +364,7 @@ typedef struct {
     int64_t steps, points, waiting, active, completed_unpolled, table_slots_used, result_rows_used;
     int64_t device_bytes;  /* physical device memory the engine's tables and rows hold now */
     int64_t refused;       /* requests completed with RASTER_E_OOM */
+    int64_t gpu_us;        /* device time of all steps so far (events around each step's work), microseconds */
 } raster_server_stats_t;
 
 /* Reserve the address ranges on the current device and start the worker

@@ -63,7 +63,7 @@ class ServerConfig(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("steps", "points", "waiting", "active", "completed_unpolled",
                                               "table_slots_used", "result_rows_used", "device_bytes",
-                                              "refused")]
+                                              "refused", "gpu_us")]
 
 
 class Clusters(ctypes.Structure):

@@ -201,6 +201,8 @@ struct raster_server {
     std::thread worker;
 
     long long steps = 0, points = 0, refused = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around each step's device work
+    double gpu_ms = 0.0;
 };
 
 namespace {
@@ -376,7 +378,7 @@ bool run_step(raster_server* s) {
     }
     if (fills.empty() && work.empty() && finishing.empty()) return false;
     cudaStream_t st = s->stream;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(s->ev0, st);
     if (!fills.empty()) {
         const int nf = (int)fills.size();
         for (int i = 0; i < nf; ++i) {
@@ -436,7 +438,10 @@ bool run_step(raster_server* s) {
         note_launch(7);
     }
     if (!e) e = cudaGetLastError();
+    if (!e) e = cudaEventRecord(s->ev1, st);
     if (!e) e = cudaStreamSynchronize(st);
+    float step_ms = 0.f;
+    if (!e) e = cudaEventElapsedTime(&step_ms, s->ev0, s->ev1);
     const Clock::time_point now = Clock::now();
     std::unique_lock<std::mutex> lk(s->mu);
     if (e != cudaSuccess) {
@@ -465,6 +470,7 @@ bool run_step(raster_server* s) {
     }
     s->steps += 1;
     s->points += pts;
+    s->gpu_ms += step_ms;
     if (na) s->cv_done.notify_all();
     return true;
 }
@@ -529,6 +535,8 @@ int raster_server_destroy(raster_server* s) {
         if (p) cudaFreeHost(p);
     s->tab_va.destroy();
     for (auto& a : s->row_va) a.destroy();
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
     if (s->stream) cudaStreamDestroy(s->stream);
     for (auto& kv : s->reqs) delete kv.second;
     delete s;
@@ -547,6 +555,8 @@ int raster_server_create(const raster_server_config* cfg, raster_server** out) {
     s->max_active = cfg->max_active;
     s->reserve = (size_t)cfg->reserve_bytes;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreate(&s->ev0);
+    if (!e) e = cudaEventCreate(&s->ev1);
     size_t free_b = 0;
     if (!e) e = cudaMemGetInfo(&free_b, &s->total_mem);
     if (!e && !s->drv.load()) e = cudaErrorNotSupported;
@@ -716,6 +726,7 @@ int raster_server_stats(raster_server* s, raster_server_stats_t* out) {
     out->result_rows_used = (int64_t)s->row_alloc.used();
     out->device_bytes = (int64_t)mapped_bytes(s);
     out->refused = s->refused;
+    out->gpu_us = (int64_t)(s->gpu_ms * 1000.0);
     return s->fatal;
 }
 
