@@ -407,7 +407,7 @@ bool run_step(raster_server* s) {
         if (!e) e = cudaMemcpyAsync(s->dc.prefix, s->hc.prefix, sizeof(long long) * (nw + 1), cudaMemcpyHostToDevice, st);
         if (!e) e = cudaMemsetAsync(s->dc.ctr, 0, sizeof(InstCounters) * nw, st);
         if (!e) {
-            k_batch_contract<2, true><<<s->g_con, 256, 0, st>>>(s->dc.inst, s->dc.prefix, nw, s->dc.ctr);
+            k_batch_contract<1, true><<<s->g_con, 256, 0, st>>>(s->dc.inst, s->dc.prefix, nw, s->dc.ctr);
             note_launch(1);
             e = cudaMemcpyAsync(s->hc.ctr, s->dc.ctr, sizeof(InstCounters) * nw, cudaMemcpyDeviceToHost, st);
         }
@@ -605,7 +605,7 @@ int raster_server_create(const raster_server_config* cfg, raster_server** out) {
     s->tab_alloc.init(s->tab_va.bytes() / sizeof(Slot));
     s->row_alloc.init(row_cap);
     s->row_capacity = (long long)row_cap;
-    s->g_con = grid_for_kernel((const void*)k_batch_contract<2, true>, 256);
+    s->g_con = grid_for_kernel((const void*)k_batch_contract<1, true>, 256);
     s->g_sel = grid_for_kernel((const void*)k_batch_select, kScanBlock);
     s->g_agg = grid_for_kernel((const void*)k_batch_hook, kAggBlock);
     s->worker = std::thread(worker_main, s);
