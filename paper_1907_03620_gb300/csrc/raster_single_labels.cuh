@@ -71,9 +71,16 @@ __device__ __forceinline__ unsigned long long lidx_mix(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
+// Home bucket of a block: its region's share, at a 32-bit hash of the block
+// (multiplicative combine of the two 24-bit fields, then xor-shift-multiply
+// rounds) scaled to the share (shares hold fewer than 2^32 buckets).
 __device__ __forceinline__ unsigned long long lidx_home(unsigned long long key, unsigned long long bk,
                                                         const RegionTable& t, unsigned long long share) {
-    return (unsigned long long)region_of(key, t) * share + __umul64hi(lidx_mix(bk), share);
+    unsigned int h = ((unsigned int)(bk >> 24) * 0x9E3779B1u) ^ ((unsigned int)(bk & 0xFFFFFFull) * 0x85EBCA77u);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    return (unsigned long long)region_of(key, t) * share + __umulhi(h, (unsigned int)share);
 }
 
 // A kept tile's code: the offset from its block's corner to its cluster id,
