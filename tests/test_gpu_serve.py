@@ -185,4 +185,6 @@ def test_served_mix_bit_exact_against_stored_oracle():
             ref, _ = oracle.raster(dev[j].cpu().numpy(), w.precision, w.tau, w.mu)
             _same(res, ref)
             pytest.fail(f"request {j} differs from the stored oracle digest")
+    st = srv.stats()
+    assert st["gpu_us"] > 0 and st["steps"] > 0 and st["refused"] == 0
     srv.close()
