@@ -44,19 +44,21 @@ POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 # (`--points 100000000`: 1.6 GB of points, a 91M-slot table).  The traffic
 # grows with the points (16 B read, keys staged twice) and with the table
 # slots (each written once), so it scales to a full launch as
-# per_point * n + per_slot * slots.  Valid only for the kernel sources it was
-# measured with (their digest); reported as null otherwise.
-MEASURED_CONTRACT_TRAFFIC = {"sources": "4fc09f4e6912edf7", "case_points": 100_000_000, "case_slots": 91_226_112,
+# per_point * n + per_slot * slots.  Valid only for the contraction kernels'
+# sources it was measured with (their digest); reported as null otherwise.
+MEASURED_CONTRACT_TRAFFIC = {"sources": "6f1a362e440c8355", "case_points": 100_000_000, "case_slots": 91_226_112,
                              "per_point": 4.749e9 / 100_000_000, "per_slot": 1.394e9 / 91_226_112}
 
 
 def kernel_sources_digest() -> str:
-    import glob
+    """Digest of the sources of the contraction kernels (the device code of
+    k_part, k_bucket, k_insert_bucket and their helpers)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1907_03620_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(csrc, "raster_single.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
-        with open(f, "rb") as fh:
+    for f in ("raster_block.cuh", "raster_device.cuh", "raster_project.cuh", "raster_region.cuh",
+              "raster_single_contract.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -207,7 +209,7 @@ def praster_sample(w: gen.Workload, sample: int) -> dict:
     xy = gen.points(w, 0, min(sample, w.n))
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    res, _, secs = oracle.praster(xy, w.precision, w.tau, w.mu, threads, with_labels=True)
+    res, _, secs = oracle.praster(xy, w.precision, w.tau, w.mu, threads, with_labels=True, sort=False)
     dt = time.perf_counter() - t0
     return {"value": xy.shape[0] / dt, "unit": "points/s", "cores": threads, "kind": "P-RASTER (oracle library)",
             "sample": f"first {xy.shape[0]:,} points of the workload (contract + agglomerate + labels)",

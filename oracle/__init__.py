@@ -89,11 +89,12 @@ def _load_praster():
     return _pr_lib
 
 
-def praster(xy, precision: float, tau: int, mu: int, threads: int, with_labels: bool = False):
+def praster(xy, precision: float, tau: int, mu: int, threads: int, with_labels: bool = False, sort: bool = True):
     """P-RASTER (Sect. 3.5, Alg. 2-3) on `threads` host threads: per-thread
     maps, join, tau filter, per-slice clustering, border joins right to left,
     then (optionally) labels.  Returns (Result, labels or None, seconds as
-    {contract, agglomerate, labels})."""
+    {contract, agglomerate, labels}).  The rows come cluster by cluster;
+    sort=True puts them in (ix, iy) order, like the oracle's."""
     a = _xy(xy)
     assert a.shape[1] == 2
     L = _load_praster()
@@ -109,6 +110,9 @@ def praster(xy, precision: float, tau: int, mu: int, threads: int, with_labels: 
             L.praster_labels(h, a.ctypes.data, a.shape[0], lab.ctypes.data)
         t = np.zeros(3)
         L.praster_times(h, t.ctypes.data)
+        if sort and k:
+            o = tile_order(key)
+            key, cnt, cid = key[o], cnt[o], cid[o]
         res = Result(status=st, points=int(a.shape[0]), n_tiles=L.praster_n_tiles(h),
                      n_significant=L.praster_n_significant(h), n_clusters=L.praster_n_clusters(h),
                      key=key, count=cnt, cid=cid)

@@ -158,7 +158,7 @@ struct praster_state {
     int64_t n_tiles, n_significant, n_clusters;
     std::vector<int64_t> key, cid;
     std::vector<uint64_t> count;
-    FlatMap cid_of;  // kept tile -> cluster id (as uint64)
+    std::vector<FlatMap> cid_of;  // per key share: kept tile -> cluster id (as uint64)
     double t_contract, t_agglomerate, t_labels;
 };
 
@@ -355,28 +355,36 @@ int praster_run(praster_state *s, const double *xy, int64_t n) {
     for (auto &c : carry)
         if (c.tiles.size() >= s->mu) out.push_back(std::move(c));
 
-    // rows with cluster ids, (ix, iy) order
-    std::vector<std::pair<int64_t, int64_t>> rows;
-    for (auto &c : out) {
-        int64_t id = c.tiles[0];
-        for (int64_t k : c.tiles)
-            if (lexless(k, id)) id = k;
-        for (int64_t k : c.tiles) rows.push_back({k, id});
-    }
-    std::sort(rows.begin(), rows.end(), [](const std::pair<int64_t, int64_t> &a, const std::pair<int64_t, int64_t> &b) {
-        return lexless(a.first, b.first);
+    // rows with cluster ids, cluster by cluster (the caller sorts them when it
+    // needs an order); ids, counts and the label map are filled in parallel
+    std::vector<size_t> first(out.size() + 1, 0);
+    for (size_t c = 0; c < out.size(); ++c) first[c + 1] = first[c] + out[c].tiles.size();
+    const size_t R = first.back();
+    s->key.resize(R);
+    s->cid.resize(R);
+    s->count.resize(R);
+    parallel(T, [&](int t) {
+        for (size_t c = out.size() * t / T; c < out.size() * (t + 1) / T; ++c) {
+            int64_t id = out[c].tiles[0];
+            for (int64_t k : out[c].tiles)
+                if (lexless(k, id)) id = k;
+            size_t r = first[c];
+            for (int64_t k : out[c].tiles) {
+                s->key[r] = k;
+                s->cid[r] = id;
+                s->count[r] = *joined[(int)(mix(k) % (uint64_t)T)].find(k);
+                ++r;
+            }
+        }
     });
-    s->key.resize(rows.size());
-    s->cid.resize(rows.size());
-    s->count.resize(rows.size());
-    s->cid_of = FlatMap(rows.size());
-    for (size_t r = 0; r < rows.size(); ++r) {
-        s->key[r] = rows[r].first;
-        s->cid[r] = rows[r].second;
-        s->cid_of.get(rows[r].first) = (uint64_t)rows[r].second;
-        const auto &m = joined[(int)(mix(rows[r].first) % (uint64_t)T)];
-        s->count[r] = *m.find(rows[r].first);
-    }
+    // label map: thread t holds the kept tiles of its key share
+    s->cid_of.assign(T, FlatMap());
+    parallel(T, [&](int t) {
+        FlatMap m(R / T + 16);
+        for (size_t r = 0; r < R; ++r)
+            if ((int)(mix(s->key[r]) % (uint64_t)T) == t) m.get(s->key[r]) = (uint64_t)s->cid[r];
+        s->cid_of[t] = std::move(m);
+    });
     s->n_clusters = (int64_t)out.size();
     s->t_agglomerate = now() - t1;
     return s->status;
@@ -395,7 +403,7 @@ int praster_labels(praster_state *s, const double *xy, int64_t n, int64_t *label
                 bad[t] = 1;
                 continue;
             }
-            const uint64_t *c = s->cid_of.find(k);
+            const uint64_t *c = s->cid_of[(int)(mix(k) % (uint64_t)T)].find(k);
             labels[i] = c ? (int64_t)*c : NOISE;
         }
     });

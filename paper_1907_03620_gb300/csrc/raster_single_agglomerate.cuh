@@ -163,11 +163,14 @@ __global__ void __launch_bounds__(kBlock) k_hook(const unsigned long long* d_nsi
         // are spread over kHookStreams streams kHookSpacing chunks apart, so
         // that the blocks in flight hook into different clusters' roots while
         // each stream still walks the table in order.
-        const long long G = (long long)kHookStreams * kHookSpacing;
-        const long long nch = (S + kBlock - 1) / kBlock, nclaims = (nch + G - 1) / G * G;
+        // (fewer rows than kHookStreams * kHookSpacing chunks: the streams close up,
+        // so that a small table makes no more claims than it has chunks, about)
+        const long long nch = (S + kBlock - 1) / kBlock;
+        const long long P = max(1ll, min(kHookSpacing, (nch + kHookStreams - 1) / kHookStreams));
+        const long long G = kHookStreams * P, nclaims = (nch + G - 1) / G * G;
         for (long long q = next_chunk(work, &s_chunk) / kBlock; q < nclaims; q = next_chunk(work, &s_chunk) / kBlock) {
             const long long w = q % G;
-            const long long c = ((q - w) + (w % kHookStreams) * kHookSpacing + w / kHookStreams) * kBlock;
+            const long long c = ((q - w) + (w % kHookStreams) * P + w / kHookStreams) * kBlock;
             if (c >= S) continue;  // the last group's claims beyond the rows
             const long long i = c + threadIdx.x;
             if (i >= S) continue;
