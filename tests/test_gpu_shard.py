@@ -111,3 +111,19 @@ def test_two_ranks_equal_the_oracle():
     o = oracle.tile_order(key)
     assert np.array_equal(key[o], ref.key) and np.array_equal(cnt[o], ref.count.astype(np.int64))
     assert np.array_equal(cid[o], ref.cid) and n_clusters == ref.n_clusters
+
+
+def test_contract_tiles_three_coordinates():
+    """Counted 3-D tiles (21-bit fields) give the clusters of the points."""
+    g = np.random.default_rng(8)
+    xyz = np.concatenate([g.uniform(0, 0.3, (60000, 3)), g.uniform(-1, 1, (20000, 3))])
+    keys, ok = oracle.project(xyz, oracle.scale_of(2))
+    k, c = np.unique(keys[ok], return_counts=True)
+    h = R.Raster(2, 3, 2, dims=3)
+    h.contract_tiles(torch.from_numpy(k).cuda(), torch.from_numpy(c.astype(np.int32)).cuda())
+    got = h.agglomerate().sorted()
+    ref, _ = oracle.raster(xyz, 2, 3, 2)
+    assert got.key.cpu().numpy().tolist() == ref.key.tolist()
+    assert got.cid.cpu().numpy().tolist() == ref.cid.tolist()
+    assert got.n_clusters == ref.n_clusters
+    h.close()
