@@ -16,7 +16,7 @@
 namespace raster {
 namespace {
 
-constexpr long long kChunkPoints = 2048;  // points per contraction work item
+constexpr long long kChunkPoints = 512;  // points per contraction work item
 constexpr long long kSlotChunk = 2048;    // table slots per select work item
 constexpr unsigned long long kMinTable = 4096;
 constexpr int kAggBlock = 256;
