@@ -39,7 +39,8 @@ TILE_BYTES = 12          # algorithmic bytes per distinct tile (key + count writ
 POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 
 # DRAM bytes (read + write) of one contraction phase (k_part, k_region_items,
-# k_bucket and k_insert_bucket) in a steady-state step, from one ncu capture
+# k_bucket and k_insert_fresh, the pass 2 of a round into a table void since
+# its reset) in a steady-state step, from one ncu capture
 # with one pass per launch on the 100M-point case of the same workload
 # (`--points 100000000`: 1.6 GB of points, a 91M-slot table).  The traffic
 # grows with the points (16 B read, keys staged twice) and with the table
@@ -52,7 +53,7 @@ MEASURED_CONTRACT_TRAFFIC = {"sources": "6f1a362e440c8355", "case_points": 100_0
 
 def kernel_sources_digest() -> str:
     """Digest of the sources of the contraction kernels (the device code of
-    k_part, k_bucket, k_insert_bucket and their helpers)."""
+    k_part, k_bucket, k_insert_fresh, k_insert_bucket and their helpers)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1907_03620_gb300", "csrc")
     h = hashlib.sha256()
@@ -545,7 +546,7 @@ def run_gpu(args):
     traffic = None
     if kernel_sources_digest() == MEASURED_CONTRACT_TRAFFIC["sources"]:
         traffic = round(MEASURED_CONTRACT_TRAFFIC["per_point"] * w.n + MEASURED_CONTRACT_TRAFFIC["per_slot"] * r.capacity)
-    roofline = {"bound": "hbm", "kernel": "contraction phase: k_part + k_region_items + k_bucket + k_insert_bucket",
+    roofline = {"bound": "hbm", "kernel": "contraction phase: k_part + k_region_items + k_bucket + k_insert_fresh",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"] + " (copy bandwidth)",
                 "traffic": traffic,

@@ -396,6 +396,7 @@ constexpr double kBucketRound = 0.25;            // rounds of fewer points per t
 constexpr double kRefitRatio = 1.5;              // a grown table this much larger than needed is rebuilt
 constexpr double kPreGrow = 4.0;                 // grow before a round whose estimate is this far past kMaxLoad
 constexpr bool kLabelsQueued = true;             // labels with the block index: k_labels_idx (queued fallbacks)
+constexpr bool kInsertSplit = true;              // pass 2 into a void table: split key/count buckets (k_insert_fresh)
 
 // One contraction round of n points: pass 1, item prefix, pass 1b, pass 2
 // (all asynchronous), then one synchronisation to read the table's tile count
@@ -503,12 +504,30 @@ int round_finish(raster_handle* h, long long n) {
         static int gi = grid_for((const void*)k_insert_bucket<false>, kInsBlock, bsmem);
         const unsigned int probe = insert_probe(h, kBucketProbe);
         auto ins = probe < kBucketProbe ? k_insert_bucket<true> : k_insert_bucket<false>;
+        const size_t fsmem = (sizeof(unsigned long long) + sizeof(unsigned int)) * kBucketSlots;
+        static bool fattr = false;
+        if (kInsertSplit && !fattr) {
+            RCHECK(h, cudaFuncSetAttribute(k_insert_fresh<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)fsmem));
+            RCHECK(h, cudaFuncSetAttribute(k_insert_fresh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)fsmem));
+            fattr = true;
+        }
+        static int gf = kInsertSplit ? grid_for((const void*)k_insert_fresh<false>, kInsBlock, fsmem) : 0;
+        auto ins_fresh = probe < kBucketProbe ? k_insert_fresh<true> : k_insert_fresh<false>;
         k_bucket<<<gb, kBlock, kBucketSmem, h->stream>>>(t, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
                                                          h->stage2, seg2, h->bcursor, h->ovf_key, h->ovf_cnt,
                                                          h->d_ctr + 5, h->d_work);
-        ins<<<(int)std::min<unsigned long long>((unsigned long long)gi, n_buckets), kInsBlock, bsmem, h->stream>>>(
-            h->tab, n_buckets, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0, (unsigned int)(kNewLimit * kBucketSlots),
-            probe, h->d_ctr, h->d_ctr + 6, h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
+        if (kInsertSplit && h->fresh)
+            ins_fresh<<<(int)std::min<unsigned long long>((unsigned long long)gf, n_buckets), kInsBlock, fsmem,
+                        h->stream>>>(h->tab, n_buckets, h->stage2, seg2, h->bcursor,
+                                     (unsigned int)(kNewLimit * kBucketSlots), probe, h->d_ctr, h->d_ctr + 6,
+                                     h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
+        else
+            ins<<<(int)std::min<unsigned long long>((unsigned long long)gi, n_buckets), kInsBlock, bsmem, h->stream>>>(
+                h->tab, n_buckets, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0,
+                (unsigned int)(kNewLimit * kBucketSlots), probe, h->d_ctr, h->d_ctr + 6, h->ovf_key, h->ovf_cnt,
+                h->d_ctr + 5, h->d_work + 1);
         h->fresh = false;  // every bucket has been written
         note_launch(3);
         RCHECK(h, cudaGetLastError());

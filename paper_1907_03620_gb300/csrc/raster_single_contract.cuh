@@ -104,30 +104,35 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double* __restrict__ x
     for (long long t0 = (long long)blockIdx.x * kPartTile; t0 < n; t0 += (long long)gridDim.x * kPartTile) {
         for (int r = threadIdx.x; r < R; r += kBlock) s_fill[r] = 0u;
         __syncthreads();
-        // two coordinates: all of the thread's loads in flight before projecting;
-        // three: loaded where projected (registers)
-        PointIn<DIMS> p[DIMS == 2 ? kPartPer : 1];
-        if (DIMS == 2) {
-#pragma unroll
-            for (int k = 0; k < kPartPer; ++k) {
-                const long long idx = t0 + k * kBlock + threadIdx.x;
-                if (idx < n) p[DIMS == 2 ? k : 0] = load_point<DIMS>(xy, idx);
-            }
-        }
+        // two coordinates: half of the thread's loads in flight before projecting
+        // that half (all of them at once spill registers); three: loaded where
+        // projected
         unsigned long long key[kPartPer];
         unsigned int meta[kPartPer];
 #pragma unroll
-        for (int k = 0; k < kPartPer; ++k) {
-            const long long idx = t0 + k * kBlock + threadIdx.x;
-            meta[k] = 0xFFFFFFFFu;
-            key[k] = 0ull;
-            if (idx < n) {
-                key[k] = project_in<WIDE, DIMS>(DIMS == 2 ? p[DIMS == 2 ? k : 0] : load_point<DIMS>(xy, idx), pp);
-                if (key[k] == kInvalidKey) {
-                    st |= kStRange;
-                } else {
-                    const unsigned int r = region_of(key[k], t);
-                    meta[k] = (r << 12) | atomicAdd(&s_fill[r], 1u);
+        for (int h = 0; h < 2; ++h) {
+            PointIn<DIMS> p[DIMS == 2 ? kPartPer / 2 : 1];
+            if (DIMS == 2) {
+#pragma unroll
+                for (int k = 0; k < kPartPer / 2; ++k) {
+                    const long long idx = t0 + (h * (kPartPer / 2) + k) * kBlock + threadIdx.x;
+                    if (idx < n) p[DIMS == 2 ? k : 0] = load_point<DIMS>(xy, idx);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kPartPer / 2; ++k) {
+                const int kk = h * (kPartPer / 2) + k;
+                const long long idx = t0 + kk * kBlock + threadIdx.x;
+                meta[kk] = 0xFFFFFFFFu;
+                key[kk] = 0ull;
+                if (idx < n) {
+                    key[kk] = project_in<WIDE, DIMS>(DIMS == 2 ? p[DIMS == 2 ? k : 0] : load_point<DIMS>(xy, idx), pp);
+                    if (key[kk] == kInvalidKey) {
+                        st |= kStRange;
+                    } else {
+                        const unsigned int r = region_of(key[kk], t);
+                        meta[kk] = (r << 12) | atomicAdd(&s_fill[r], 1u);
+                    }
                 }
             }
         }
@@ -336,6 +341,23 @@ __device__ __forceinline__ bool bucket_add(Slot* s_tab, unsigned long long key, 
     return false;
 }
 
+// bucket_add on a bucket held as separate key and count arrays.
+template <bool LIMITED>
+__device__ __forceinline__ bool bucket_add_split(unsigned long long* s_key, unsigned int* s_cnt,
+                                                 unsigned long long key, unsigned int max_probe) {
+    unsigned int i = tile_hash(key) & (kBucketSlots - 1u);
+    for (unsigned int p = 0; p < (LIMITED ? max_probe : kBucketProbe); ++p) {
+        unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s_key[i]);
+        if (k == kEmptyKey) k = atomicCAS(&s_key[i], kEmptyKey, key);
+        if (k == kEmptyKey || k == key) {
+            atomicAdd(&s_cnt[i], 1u);
+            return true;
+        }
+        i = (i + 1u) & (kBucketSlots - 1u);
+    }
+    return false;
+}
+
 // Pass 2 of contraction: one bucket at a time per block.  The bucket's slots
 // are copied to shared memory (or cleared, for the first round after a reset,
 // when the table's contents are void), its staged keys are inserted there with
@@ -439,6 +461,98 @@ __global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ 
         if (threadIdx.x == 0) {
             if (s_occ1 > s_occ0) atomicAdd(d_newkeys, (unsigned long long)(s_occ1 - s_occ0));
             const unsigned int over = s_nfull + (s_occ1 > limit ? 1u : 0u);
+            if (over) atomicAdd(d_full, (unsigned long long)over);
+        }
+    }
+}
+
+// Pass 2 for the first round into a void table (after a reset): as
+// k_insert_bucket, but the bucket is cleared rather than loaded, and held as
+// separate key and count arrays (48 KiB instead of 64 KiB: four blocks of
+// kInsBlock threads per SM instead of three); it is written back as whole
+// slots with aux none.  Every bucket is written, so the table needs no fill.
+template <bool LIMITED>
+__global__ void __launch_bounds__(kInsBlock, 4)
+    k_insert_fresh(Slot* __restrict__ tab, unsigned long long n_buckets, const unsigned long long* __restrict__ stage2,
+                   unsigned long long seg2, const unsigned int* __restrict__ bcursor, unsigned int limit,
+                   unsigned int max_probe, unsigned long long* d_newkeys, unsigned long long* d_full,
+                   unsigned long long* ovf_key, unsigned int* ovf_cnt, unsigned long long* ovf_n,
+                   unsigned long long* work) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(smem);     // kBucketSlots keys
+    unsigned int* s_cnt = reinterpret_cast<unsigned int*>(s_key + kBucketSlots);  // kBucketSlots counts
+    __shared__ unsigned int s_occ, s_nfull;
+    __shared__ int s_full;
+    __shared__ unsigned long long s_b;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        // the previous bucket's write-back ended at a barrier
+        if (threadIdx.x == 0) {
+            s_b = atomicAdd(work, 1ull);
+            s_occ = 0u;
+            s_nfull = 0u;
+            s_full = 0;
+        }
+        {
+            ulonglong2 e;
+            e.x = kEmptyKey;
+            e.y = kEmptyKey;
+            for (unsigned int i = threadIdx.x; i < kBucketSlots / 2; i += kInsBlock)
+                reinterpret_cast<ulonglong2*>(s_key)[i] = e;
+            for (unsigned int i = threadIdx.x; i < kBucketSlots / 4; i += kInsBlock)
+                reinterpret_cast<uint4*>(s_cnt)[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        const unsigned long long b = s_b;
+        if (b >= n_buckets) break;
+        const unsigned long long n = min((unsigned long long)bcursor[b], seg2);
+        const unsigned long long* keys = stage2 + b * seg2;
+        unsigned int full = 0;
+        for (unsigned long long j0 = 0; j0 < n; j0 += (unsigned long long)kInsBlock * kInsertUnroll) {
+            unsigned long long kk[kInsertUnroll];
+#pragma unroll
+            for (int u = 0; u < kInsertUnroll; ++u) {
+                const unsigned long long j = j0 + (unsigned long long)(u * kInsBlock + threadIdx.x);
+                kk[u] = j < n ? __ldcs(keys + j) : kInvalidKey;
+            }
+#pragma unroll
+            for (int u = 0; u < kInsertUnroll; ++u) {
+                bool spill = false;
+                if (kk[u] != kInvalidKey) {
+                    if (*reinterpret_cast<volatile int*>(&s_full) ||
+                        !bucket_add_split<LIMITED>(s_key, s_cnt, kk[u], max_probe)) {
+                        spill = true;
+                        s_full = 1;
+                        ++full;
+                    }
+                }
+                if (__any_sync(0xFFFFFFFFu, spill)) overflow_append(spill, kk[u], 1u, ovf_key, ovf_cnt, ovf_n);
+            }
+        }
+        full = __reduce_add_sync(0xFFFFFFFFu, full);
+        if (lane == 0 && full) atomicAdd(&s_nfull, full);
+        __syncthreads();
+        // two slots per thread and step: one 16-byte and one 8-byte shared load, two 16-byte stores
+        ulonglong2* g = reinterpret_cast<ulonglong2*>(tab + (b << kBucketBits));
+        unsigned int occ = 0;
+        for (unsigned int i = threadIdx.x; i < kBucketSlots / 2; i += kInsBlock) {
+            const ulonglong2 k2 = reinterpret_cast<const ulonglong2*>(s_key)[i];
+            const uint2 c2 = reinterpret_cast<const uint2*>(s_cnt)[i];
+            ulonglong2 v0, v1;
+            v0.x = k2.x;
+            v0.y = ((unsigned long long)kAuxNone << 32) | c2.x;
+            v1.x = k2.y;
+            v1.y = ((unsigned long long)kAuxNone << 32) | c2.y;
+            occ += (k2.x != kEmptyKey) + (k2.y != kEmptyKey);
+            g[2 * i] = v0;
+            g[2 * i + 1] = v1;
+        }
+        occ = __reduce_add_sync(0xFFFFFFFFu, occ);
+        if (lane == 0 && occ) atomicAdd(&s_occ, occ);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_occ) atomicAdd(d_newkeys, (unsigned long long)s_occ);
+            const unsigned int over = s_nfull + (s_occ > limit ? 1u : 0u);
             if (over) atomicAdd(d_full, (unsigned long long)over);
         }
     }
