@@ -171,14 +171,12 @@ __global__ void k_lidx_build(const unsigned long long* d_nkept, const unsigned l
     }
 }
 
-// Label of a valid two-coordinate key from the block index: true with *lab
-// set (a cluster id or noise), false when the tile table has to answer.
-__device__ __forceinline__ bool lidx_label(const LabelIndex& li, const RegionTable& t, unsigned long long key,
-                                           long long* lab) {
-    unsigned long long bk;
-    if (!lidx_block(key, &bk)) return false;
-    unsigned long long b = lidx_home(key, bk, t, li.share);
-    for (unsigned int p = 0; p < kLidxProbe; ++p) {
+// Label of a valid two-coordinate key of block bk from the block index,
+// searching from bucket b on (at most `probes` buckets): true with *lab set
+// (a cluster id or noise), false when the tile table has to answer.
+__device__ __forceinline__ bool lidx_label_from(const LabelIndex& li, unsigned long long key, unsigned long long bk,
+                                                unsigned long long b, unsigned int probes, long long* lab) {
+    for (unsigned int p = 0; p < probes; ++p) {
         const ulonglong4 v = lidx_load(li.ent + 4 * b);
         unsigned long long w, w1;  // the entry: code word, kept mask
         if ((v.x >> 16) == bk) {
@@ -206,6 +204,14 @@ __device__ __forceinline__ bool lidx_label(const LabelIndex& li, const RegionTab
         return true;
     }
     return false;
+}
+
+// The same from the block's home bucket.
+__device__ __forceinline__ bool lidx_label(const LabelIndex& li, const RegionTable& t, unsigned long long key,
+                                           long long* lab) {
+    unsigned long long bk;
+    if (!lidx_block(key, &bk)) return false;
+    return lidx_label_from(li, key, bk, lidx_home(key, bk, t, li.share), kLidxProbe, lab);
 }
 
 template <bool WIDE, int DIMS>
@@ -238,13 +244,19 @@ __global__ void k_labels(const double* __restrict__ xy, long long n, ProjParams 
 // and the table behind it, with every lane busy.  Answering them where they
 // arise left most lanes of a warp idle while a few probed on.
 constexpr int kLabQueue = 64;  // per warp: up to 31 waiting plus 32 new
+constexpr long long kQueueTable = 1ll << 62;  // queued point that only the tile table can answer
 
-// 1 with *lab set when the home bucket answers; 0 when the full lookup must.
+// What the home bucket says about a key: kLidxAnswered with *lab set;
+// kLidxLater when the block may sit in a later bucket (*next: the bucket
+// after the home bucket); kLidxTable when only the tile table can answer (a
+// mixed block, or a block out of the index's range).
+constexpr int kLidxLater = 0, kLidxAnswered = 1, kLidxTable = 2;
 __device__ __forceinline__ int lidx_first(const LabelIndex& li, const RegionTable& t, unsigned long long key,
-                                          long long* lab) {
+                                          long long* lab, unsigned long long* next) {
     unsigned long long bk;
-    if (!lidx_block(key, &bk)) return 0;
-    const ulonglong4 v = lidx_load(li.ent + 4 * lidx_home(key, bk, t, li.share));
+    if (!lidx_block(key, &bk)) return kLidxTable;
+    const unsigned long long b = lidx_home(key, bk, t, li.share);
+    const ulonglong4 v = lidx_load(li.ent + 4 * b);
     unsigned long long w, w1;
     if ((v.x >> 16) == bk) {
         w = v.x;
@@ -253,19 +265,22 @@ __device__ __forceinline__ int lidx_first(const LabelIndex& li, const RegionTabl
         w = v.z;
         w1 = v.w;
     } else {
-        if (v.z != 0ull) return 0;  // the block may sit in a later bucket
+        if (v.z != 0ull) {  // the block may sit in a later bucket
+            *next = b + 1 == li.buckets ? 0 : b + 1;
+            return kLidxLater;
+        }
         *lab = (long long)kEmptyKey;
-        return 1;
+        return kLidxAnswered;
     }
     if (!((w1 >> lidx_bit(key)) & 1ull)) {
         *lab = (long long)kEmptyKey;
-        return 1;
+        return kLidxAnswered;
     }
     const unsigned int code = (unsigned int)(w & 0xFFFFull);
-    if (code == kLidxMixed) return 0;
+    if (code == kLidxMixed) return kLidxTable;
     *lab = (long long)pack_key((key_x(key) & ~7) + (int)(signed char)(code >> 8),
                                (key_y(key) & ~7) + (int)(signed char)(code & 0xFFu));
-    return 1;
+    return kLidxAnswered;
 }
 
 template <bool WIDE>
@@ -274,7 +289,8 @@ __global__ void __launch_bounds__(kBlock) k_labels_idx(const double* __restrict_
                                                       long long* __restrict__ labels, unsigned int* d_status,
                                                       LabelIndex li) {
     __shared__ unsigned long long s_key[kBlock / 32][kLabQueue];
-    __shared__ long long s_idx[kBlock / 32][kLabQueue];
+    __shared__ long long s_idx[kBlock / 32][kLabQueue];            // point, with kQueueTable for the table
+    __shared__ unsigned long long s_next[kBlock / 32][kLabQueue];  // the bucket to search from
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool index_ok = *li.bad == 0u;
     const long long warps_total = (long long)gridDim.x * (kBlock / 32);
@@ -284,9 +300,13 @@ __global__ void __launch_bounds__(kBlock) k_labels_idx(const double* __restrict_
     auto drain = [&](int count) {
         if (lane < count) {
             const unsigned long long key = s_key[warp][qn - count + lane];
-            const long long i = s_idx[warp][qn - count + lane];
+            const long long qi = s_idx[warp][qn - count + lane];
+            const long long i = qi & ~kQueueTable;
             long long lab = (long long)kEmptyKey;
-            if (!(index_ok && lidx_label(li, t, key, &lab))) {
+            unsigned long long bk;
+            // a later bucket: the rest of the search (the home bucket was read)
+            if (!(index_ok && !(qi & kQueueTable) && lidx_block(key, &bk) &&
+                  lidx_label_from(li, key, bk, s_next[warp][qn - count + lane], kLidxProbe - 1, &lab))) {
                 const Slot sl = rt_get(t, key);
                 if (sl.key == key) lab = label_decode(key, sl.aux, cid_rows);  // kAuxNone decodes to noise
             }
@@ -297,25 +317,27 @@ __global__ void __launch_bounds__(kBlock) k_labels_idx(const double* __restrict_
     };
     for (long long base = ((long long)blockIdx.x * (kBlock / 32) + warp) * 32; base < n; base += warps_total * 32) {
         const long long i = base + lane;
-        unsigned long long key = kInvalidKey;
+        unsigned long long key = kInvalidKey, next = 0;
         long long lab = (long long)kEmptyKey;
         bool defer = false, have = false;
+        int mode = kLidxTable;
         if (i < n) {
             key = project_in<WIDE, 2>(load_point<2>(xy, i), pp);
             if (key == kInvalidKey) {
                 st |= kStRange;
                 have = true;
-            } else if (index_ok && lidx_first(li, t, key, &lab)) {
-                have = true;
             } else {
-                defer = true;
+                if (index_ok) mode = lidx_first(li, t, key, &lab, &next);
+                have = mode == kLidxAnswered;
+                defer = !have;
             }
         }
         const unsigned int m = __ballot_sync(0xFFFFFFFFu, defer);
         if (defer) {
             const int pos = qn + __popc(m & ((1u << lane) - 1u));
             s_key[warp][pos] = key;
-            s_idx[warp][pos] = i;
+            s_idx[warp][pos] = mode == kLidxTable ? (i | kQueueTable) : i;
+            s_next[warp][pos] = next;
         }
         qn += __popc(m);
         __syncwarp();
