@@ -432,7 +432,7 @@ int round_begin(raster_handle* h, long long n) {
 template <bool WIDE>
 int round_part(raster_handle* h, const double* xy, long long m) {
     if (m <= 0) return RASTER_OK;
-    const unsigned long long seg = h->stage_cap / h->regions;
+    const unsigned long long seg = (h->stage_cap / h->regions) & ~1ull;  // even: 16-byte aligned item starts
     RegionTable t = table_of(h);
     const size_t smem = part_smem(h->regions);
     const void* part = h->dims == 3 ? (const void*)k_part<WIDE, 3> : (const void*)k_part<WIDE, 2>;
@@ -461,7 +461,7 @@ int round_part(raster_handle* h, const double* xy, long long m) {
 int round_finish(raster_handle* h, long long n) {
     int rc;
     const bool grew_before = h->round_grew;
-    const unsigned long long seg = h->stage_cap / h->regions;
+    const unsigned long long seg = (h->stage_cap / h->regions) & ~1ull;  // even: 16-byte aligned item starts
     RegionTable t = table_of(h);
     k_region_items<<<1, kBlock, 0, h->stream>>>(h->cursor, (int)h->regions, seg, h->item_start);
     // pass 2: whole buckets in shared memory, unless the round is much smaller

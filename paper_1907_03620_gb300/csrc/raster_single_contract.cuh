@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double* __restrict__ x
     unsigned long long* s_sorted = reinterpret_cast<unsigned long long*>(smem);         // kPartTile keys
     unsigned int* s_fill = reinterpret_cast<unsigned int*>(s_sorted + kPartTile);       // regions
     unsigned int* s_start = s_fill + t.regions;                                         // regions
-    unsigned int* s_gbase = s_start + t.regions;                                        // regions
+    unsigned int* s_gbase = s_start + t.regions;  // regions: segment position minus tile position (mod 2^32)
     unsigned short* s_reg = reinterpret_cast<unsigned short*>(s_gbase + t.regions);     // kPartTile regions
     __shared__ unsigned int scratch[33];
     const int R = (int)t.regions;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double* __restrict__ x
         __syncthreads();
         const unsigned int total = block_excl_scan_bins(s_fill, R, s_start, scratch);
         for (int r = threadIdx.x; r < R; r += kBlock)
-            if (s_fill[r]) s_gbase[r] = atomicAdd(&cursor[r], s_fill[r]);
+            if (s_fill[r]) s_gbase[r] = atomicAdd(&cursor[r], s_fill[r]) - s_start[r];
 #pragma unroll
         for (int k = 0; k < kPartPer; ++k) {
             if (meta[k] != 0xFFFFFFFFu) {
@@ -157,13 +157,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double* __restrict__ x
             if (j < total) {
                 key = s_sorted[j];
                 const unsigned int r = s_reg[j];
-                const unsigned long long pos = (unsigned long long)s_gbase[r] + (j - s_start[r]);
+                const unsigned long long pos = s_gbase[r] + j;  // below 2^32: within the segment or just past it
                 if (pos < seg_cap)
                     stage[(unsigned long long)r * seg_cap + pos] = key;
                 else
                     spill = true;  // region far above its share: to the overflow list
             }
-            overflow_append(spill, key, 1u, ovf_key, ovf_cnt, ovf_n);
+            if (__any_sync(0xFFFFFFFFu, spill)) overflow_append(spill, key, 1u, ovf_key, ovf_cnt, ovf_n);
         }
         __syncthreads();
     }
@@ -246,15 +246,19 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
         }
         __syncthreads();
         if (s_it[q] < total) {
+            // two keys per 16-byte copy: k0 and seg_cap are even, so a pair that
+            // starts below k1 ends inside the segment (its second key may lie past
+            // k1, and is not read)
             const unsigned long long k0 = s_k0[q], k1 = s_k1[q];
             const unsigned long long* seg = stage + (unsigned long long)s_r[q] * seg_cap;
 #pragma unroll
-            for (int k = 0; k < (int)(kInsertItem / kBlock); ++k) {
-                const unsigned long long j = k0 + (unsigned long long)(k * kBlock + threadIdx.x);
+            for (int k = 0; k < (int)(kInsertItem / kBlock / 2); ++k) {
+                const unsigned int pj = 2u * (unsigned int)(k * kBlock + threadIdx.x);
+                const unsigned long long j = k0 + pj;
                 if (j < k1) {
-                    const unsigned int dst = (unsigned int)__cvta_generic_to_shared(
-                        s_in + (size_t)q * kInsertItem + k * kBlock + threadIdx.x);
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(seg + j) : "memory");
+                    const unsigned int dst =
+                        (unsigned int)__cvta_generic_to_shared(s_in + (size_t)q * kInsertItem + pj);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(seg + j) : "memory");
                 }
             }
         }
@@ -288,8 +292,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
         __syncthreads();  // also: every key of s_cur is in registers
         const unsigned int n_items = block_excl_scan_bins(s_fill, NB, s_start, scratch);
         const unsigned long long g0 = (unsigned long long)r << bb;  // first bucket of region r
-        if (threadIdx.x < NB && s_fill[threadIdx.x])
-            s_gbase[threadIdx.x] = atomicAdd(&bcursor[g0 + threadIdx.x], s_fill[threadIdx.x]);
+        if (threadIdx.x < NB && s_fill[threadIdx.x])  // segment position minus item position (mod 2^32)
+            s_gbase[threadIdx.x] = atomicAdd(&bcursor[g0 + threadIdx.x], s_fill[threadIdx.x]) - s_start[threadIdx.x];
 #pragma unroll
         for (int k = 0; k < (int)(kInsertItem / kBlock); ++k) {
             if (meta[k] != 0xFFFFFFFFu) {
@@ -307,13 +311,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_bucket(RegionTable t, const unsig
             if (j < n_items) {
                 k = s_cur[j];
                 const unsigned int b = s_b[j];
-                const unsigned long long pos = (unsigned long long)s_gbase[b] + (j - s_start[b]);
+                const unsigned long long pos = s_gbase[b] + j;  // below 2^32: within the segment or just past it
                 if (pos < seg2)
                     stage2[(g0 + b) * seg2 + pos] = k;
                 else
                     spill = true;  // bucket far above its share: to the overflow list
             }
-            overflow_append(spill, k, 1u, ovf_key, ovf_cnt, ovf_n);
+            if (__any_sync(0xFFFFFFFFu, spill)) overflow_append(spill, k, 1u, ovf_key, ovf_cnt, ovf_n);
         }
         __syncthreads();
         q ^= 1;
