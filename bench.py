@@ -484,6 +484,7 @@ def run_gpu(args):
     gen.points_into(host.numpy(), w)
     xy = host.to(dev, non_blocking=False)
     labels = torch.empty(w.n, dtype=torch.int64, device=dev)
+    keys = torch.empty(w.n, dtype=torch.int64, device=dev)  # every point's tile key, written by the contraction
     stream = torch.cuda.current_stream()
 
     r = R.Raster(w.precision, w.tau, w.mu)
@@ -494,11 +495,11 @@ def run_gpu(args):
         e0.record(stream)
         r.reset()
         e1.record(stream)
-        r.contract(xy)
+        r.contract_keys(xy, keys)  # contraction, storing each point's tile key
         e2.record(stream)
         res = r.agglomerate(copy=False, raw=True)
         e3.record(stream)
-        r.point_labels(xy, out=labels)
+        r.key_labels(keys, out=labels)  # RASTER* labels read from the stored keys
         e4.record(stream)
         if record is not None:
             record.append((e0, e1, e2, e3, e4, res))
@@ -537,6 +538,20 @@ def run_gpu(args):
         phase["labels"].append(e3.elapsed_time(e4))
     res = recs[-1][5]
     ms_step = total_ms / args.steps
+    # for comparison, outside the timed steps and with the label index already
+    # built: the labels of the same points projected again from their
+    # coordinates (raster_point_labels) and read from the stored keys
+    lp_ms, lk_ms = [], []
+    for rep in range(3):
+        l0, l1, l2 = ev(), ev(), ev()
+        l0.record(stream)
+        r.point_labels(xy, out=labels)
+        l1.record(stream)
+        r.key_labels(keys, out=labels)
+        l2.record(stream)
+        torch.cuda.synchronize()
+        lp_ms.append(l0.elapsed_time(l1))
+        lk_ms.append(l1.elapsed_time(l2))
     value = whole_job_rate(world, w.n, ms_step / 1e3)
 
     peaks = measured_peaks()
@@ -553,15 +568,16 @@ def run_gpu(args):
                 "traffic_unit": ("bytes per contraction phase (ncu dram__bytes read+write on the 100M-point case, "
                                  "scaled per point and per table slot)"),
                 "algorithmic_bytes": alg_bytes, "algorithmic": "16 B/point + 12 B/distinct tile",
+                "also_stored": "8 B/point of tile keys for the labels (not counted as algorithmic bytes)",
                 "phase_ms": contract_ms}
     # the other phases of the step, against the same peak
     ag_bytes = 12 * res.n_distinct + 24 * res.n_significant + 20 * int(res.key.numel())
-    lb_bytes = 24 * w.n
+    lb_bytes = 16 * w.n
     roofline_phases = {
         "agglomerate": {"algorithmic_bytes": ag_bytes, "algorithmic": "12 B/tile + 24 B/significant + 20 B/kept row",
                         "ms": statistics.mean(phase["agglomerate"]),
                         "frac": ag_bytes / (statistics.mean(phase["agglomerate"]) / 1e3) / 1e9 / peaks["hbm_gbs"]},
-        "labels": {"algorithmic_bytes": lb_bytes, "algorithmic": "16 B/point read + 8 B/point written",
+        "labels": {"algorithmic_bytes": lb_bytes, "algorithmic": "8 B/point key read + 8 B/point label written",
                    "ms": statistics.mean(phase["labels"]),
                    "frac": lb_bytes / (statistics.mean(phase["labels"]) / 1e3) / 1e9 / peaks["hbm_gbs"]}}
 
@@ -570,6 +586,10 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(w, args.workload), parallelism=f"replicas{world}"),
             "phases_ms": {k: statistics.mean(v) for k, v in phase.items()},
+            "step": ("raster_reset; raster_contract_keys (contraction, storing each point's tile key); "
+                     "raster_agglomerate; raster_key_labels (labels read from the stored keys)"),
+            "labels_without_index_build_ms": {"from_points": statistics.mean(lp_ms[1:]),
+                                              "from_keys": statistics.mean(lk_ms[1:])},
             "stats": {"n_distinct": res.n_distinct, "n_significant": res.n_significant,
                       "n_clusters": res.n_clusters, "kept_tiles": int(res.key.numel()),
                       "table_slots": r.capacity, "table": r.table_stats()},
@@ -586,9 +606,9 @@ def run_gpu(args):
             c0.record(stream)
             r.reset()
             for c in range(10):
-                r.contract(xy[c * m:(c + 1) * m])
+                r.contract_keys(xy[c * m:(c + 1) * m], keys[c * m:(c + 1) * m])
             r.agglomerate(copy=False, raw=True)
-            r.point_labels(xy, out=labels)
+            r.key_labels(keys, out=labels)
             c1.record(stream)
             torch.cuda.synchronize()
             if rep:
@@ -634,11 +654,11 @@ def run_gpu(args):
                 e0, e1, e2, e3 = ev(), ev(), ev(), ev()
                 e0.record(stream)
                 rx.reset()
-                rx.contract(xy)
+                rx.contract_keys(xy, keys)
                 e1.record(stream)
                 resx = rx.agglomerate(copy=False, raw=True)
                 e2.record(stream)
-                rx.point_labels(xy, out=labels)
+                rx.key_labels(keys, out=labels)
                 e3.record(stream)
                 torch.cuda.synchronize()
                 if rep:
@@ -657,17 +677,18 @@ def run_gpu(args):
         xyz = torch.from_numpy(gen.cubes3(**c3)).to(dev)
         n3 = xyz.shape[0]
         lab3 = torch.empty(n3, dtype=torch.int64, device=dev)
+        key3 = torch.empty(n3, dtype=torch.int64, device=dev)
         r3 = R.Raster(1.5, 5, 4, dims=3)
         times = {"contract": [], "agglomerate": [], "labels": []}
         for rep in range(4):
             e0, e1, e2, e3 = ev(), ev(), ev(), ev()
             e0.record(stream)
             r3.reset()
-            r3.contract(xyz)
+            r3.contract_keys(xyz, key3)
             e1.record(stream)
             res3 = r3.agglomerate(copy=False, raw=True)
             e2.record(stream)
-            r3.point_labels(xyz, out=lab3)
+            r3.key_labels(key3, out=lab3)
             e3.record(stream)
             torch.cuda.synchronize()
             if rep:
@@ -682,7 +703,7 @@ def run_gpu(args):
             "n_distinct": res3.n_distinct, "n_significant": res3.n_significant, "n_clusters": res3.n_clusters,
             "contraction_frac": (24 * n3 + 12 * res3.n_distinct) / (ms["contract"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
         r3.close()
-        del xyz, lab3
+        del xyz, lab3, key3
         line["extensions"] = ext
 
     # e2e: host buffers through the C ABI, copies inside the timed region: one

@@ -58,6 +58,7 @@ extern "C" {
 #define RASTER_E_LIMIT 8       /* input larger than a fixed capacity (raster_count_tiles_static) */
 
 #define RASTER_NOISE INT64_MIN /* label of a point outside every kept cluster */
+#define RASTER_INVALID_KEY (INT64_MIN + 1) /* tile key of a point that did not project (raster_contract_keys) */
 
 typedef struct raster_handle raster_handle;
 
@@ -142,6 +143,18 @@ int raster_reserve(raster_handle *h, int64_t n_tiles);
  * must stay below 2^32. */
 int raster_contract(raster_handle *h, const double *xy, int64_t n, void *stream);
 
+/* Contraction as raster_contract (Alg. 1 first loop; the projection of
+ * Sect. 3.2), which also writes each point's tile key, so that the labels of
+ * the same points can later be read from the keys (raster_key_labels)
+ * instead of projecting every point a second time.
+ * keys: DEVICE int64[n], 8-byte aligned, caller-owned; keys[i] is the tile of
+ * point i in the handle's packing, or RASTER_INVALID_KEY for a point with a
+ * non-finite coordinate or a tile index out of range (those points are
+ * skipped and reported as RASTER_E_RANGE, as by raster_contract).
+ * Asynchronous like raster_contract; keys are complete when the stream
+ * reaches the end of the call. */
+int raster_contract_keys(raster_handle *h, const double *xy, int64_t n, int64_t *keys, void *stream);
+
 /* Add tiles counted elsewhere: count[i] points to tile key[i], as if those
  * points had been contracted into this handle.  This is the join of partial
  * count maps that P-RASTER performs after its parallel contraction (Sect.
@@ -181,6 +194,17 @@ int raster_agglomerate(raster_handle *h, raster_clusters *out);
  * RASTER_LABEL_INDEX, read when the handle is created, forces that index on
  * ("1") or off ("0"); the labels are the same either way. */
 int raster_point_labels(raster_handle *h, const double *xy, int64_t n, int64_t *labels, void *stream);
+
+/* Per-point cluster labels (RASTER*, Sect. 4.1) from the points' tile keys,
+ * as written by raster_contract_keys into this handle: the same labels that
+ * raster_point_labels gives for those points, without reading or projecting
+ * the coordinates again.  Requires a preceding raster_agglomerate with no
+ * contract since.  keys: DEVICE int64[n] (8-byte aligned; any key of the
+ * handle's packing is accepted; RASTER_INVALID_KEY is labelled RASTER_NOISE
+ * and raises the handle's range flag, as a non-finite point does in
+ * raster_point_labels); labels: DEVICE int64[n], caller-owned.  Asynchronous,
+ * with the same one-time synchronisation as raster_point_labels. */
+int raster_key_labels(raster_handle *h, const int64_t *keys, int64_t n, int64_t *labels, void *stream);
 
 /* Per-point labels (RASTER*, Sect. 4.1) as raster_point_labels, with HOST xy
  * and HOST labels; synchronous. */

@@ -17,7 +17,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _native
-from ._native import CHEBYSHEV, MANHATTAN, NOISE, RasterError, check, lib
+from ._native import CHEBYSHEV, INVALID_KEY, MANHATTAN, NOISE, RasterError, check, lib
 
 __all__ = ["Raster", "Result", "RasterError", "NOISE", "CHEBYSHEV", "MANHATTAN", "lib", "build", "pack", "unpack",
            "pack3", "unpack3"]
@@ -163,6 +163,19 @@ class Raster:
         check(self._L.raster_contract(self._h, ctypes.c_void_p(xy.data_ptr()), xy.shape[0], _stream_ptr(stream)),
               "raster_contract")
 
+    def contract_keys(self, xy: torch.Tensor, keys: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """contract(xy), also writing each point's tile key (CUDA int64, n
+        entries; INVALID_KEY for a point that does not project) for
+        key_labels."""
+        _check_points(xy, "contract_keys", self.dims)
+        if keys is None:
+            keys = torch.empty(xy.shape[0], dtype=torch.int64, device=xy.device)
+        assert keys.is_cuda and keys.dtype == torch.int64 and keys.is_contiguous() and keys.numel() == xy.shape[0]
+        check(self._L.raster_contract_keys(self._h, ctypes.c_void_p(xy.data_ptr()), xy.shape[0],
+                                           ctypes.c_void_p(keys.data_ptr()), _stream_ptr(stream)),
+              "raster_contract_keys")
+        return keys
+
     def contract_tiles(self, key: torch.Tensor, count: torch.Tensor, stream=None):
         """Add count[i] points to tile key[i] (CUDA int64 keys, CUDA int32 or
         uint32-valued counts): the join of partial tile counts."""
@@ -233,6 +246,18 @@ class Raster:
         check(self._L.raster_point_labels(self._h, ctypes.c_void_p(xy.data_ptr()), xy.shape[0],
                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
               "raster_point_labels")
+        return out
+
+    def key_labels(self, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Labels of the points whose tile keys contract_keys wrote: the same
+        as point_labels of those points."""
+        assert keys.is_cuda and keys.dtype == torch.int64 and keys.is_contiguous()
+        if out is None:
+            out = torch.empty(keys.numel(), dtype=torch.int64, device=keys.device)
+        assert out.is_cuda and out.dtype == torch.int64 and out.is_contiguous() and out.numel() == keys.numel()
+        check(self._L.raster_key_labels(self._h, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                                        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+              "raster_key_labels")
         return out
 
     def point_labels_host(self, xy, out=None, stream=None):

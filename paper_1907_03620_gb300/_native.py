@@ -20,6 +20,7 @@ OK = 0
 E_ARG, E_RANGE, E_OOM, E_TABLE_FULL, E_CUDA, E_INTERNAL, E_STATE, E_LIMIT = 1, 2, 3, 4, 5, 6, 7, 8
 STATIC_MAX_POINTS = 524288
 NOISE = -(2 ** 63)
+INVALID_KEY = -(2 ** 63) + 1  # tile key of a point that did not project (RASTER_INVALID_KEY)
 CHEBYSHEV, MANHATTAN, MAX_DELTA = 0, 1, 4  # RASTER_CHEBYSHEV, RASTER_MANHATTAN, RASTER_MAX_DELTA
 NAMES = {0: "RASTER_OK", 1: "RASTER_E_ARG", 2: "RASTER_E_RANGE", 3: "RASTER_E_OOM", 4: "RASTER_E_TABLE_FULL",
          5: "RASTER_E_CUDA", 6: "RASTER_E_INTERNAL", 7: "RASTER_E_STATE", 8: "RASTER_E_LIMIT"}
@@ -92,6 +93,8 @@ def _declare(L):
         "raster_create_ex": (ci, [ctypes.POINTER(Params), ctypes.POINTER(vp)]),
         "raster_reserve": (ci, [vp, i64]),
         "raster_contract": (ci, [vp, vp, i64, vp]),
+        "raster_contract_keys": (ci, [vp, vp, i64, vp, vp]),
+        "raster_key_labels": (ci, [vp, vp, i64, vp, vp]),
         "raster_contract_host": (ci, [vp, vp, i64, vp]),
         "raster_agglomerate": (ci, [vp, ctypes.POINTER(Clusters)]),
         "raster_contract_tiles": (ci, [vp, vp, vp, i64, vp]),

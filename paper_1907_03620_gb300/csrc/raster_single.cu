@@ -430,7 +430,7 @@ int round_begin(raster_handle* h, long long n) {
 
 // Pass 1 over m points of the round (appends to the staging segments).
 template <bool WIDE>
-int round_part(raster_handle* h, const double* xy, long long m) {
+int round_part(raster_handle* h, const double* xy, long long m, unsigned long long* keys_out = nullptr) {
     if (m <= 0) return RASTER_OK;
     const unsigned long long seg = (h->stage_cap / h->regions) & ~1ull;  // even: 16-byte aligned item starts
     RegionTable t = table_of(h);
@@ -449,10 +449,10 @@ int round_part(raster_handle* h, const double* xy, long long m) {
     const int g1 = (int)std::max<long long>(1, std::min<long long>((long long)sms * std::max(per_sm, 1), tiles));
     if (h->dims == 3)
         k_part<WIDE, 3><<<g1, kBlock, smem, h->stream>>>(xy, m, h->pp, t, h->stage_keys, seg, h->cursor, h->ovf_key,
-                                                         h->ovf_cnt, h->d_ctr + 5, h->d_status);
+                                                         h->ovf_cnt, h->d_ctr + 5, h->d_status, keys_out);
     else
         k_part<WIDE, 2><<<g1, kBlock, smem, h->stream>>>(xy, m, h->pp, t, h->stage_keys, seg, h->cursor, h->ovf_key,
-                                                         h->ovf_cnt, h->d_ctr + 5, h->d_status);
+                                                         h->ovf_cnt, h->d_ctr + 5, h->d_status, keys_out);
     note_launch();
     RCHECK(h, cudaGetLastError());
     return RASTER_OK;
@@ -571,19 +571,21 @@ int round_finish(raster_handle* h, long long n) {
 }
 
 template <bool WIDE>
-int contract_round(raster_handle* h, const double* xy, long long n) {
+int contract_round(raster_handle* h, const double* xy, long long n, unsigned long long* keys_out) {
     int rc = round_begin(h, n);
     if (rc) return rc;
-    rc = round_part<WIDE>(h, xy, n);
+    rc = round_part<WIDE>(h, xy, n, keys_out);
     if (rc) return rc;
     return round_finish(h, n);
 }
 
-int contract_device(raster_handle* h, const double* xy, long long n) {
+// keys_out (optional): every point's tile key, in point order
+int contract_device(raster_handle* h, const double* xy, long long n, unsigned long long* keys_out = nullptr) {
     for (long long off = 0; off < n; off += kRoundPoints) {
         const long long m = std::min(n - off, kRoundPoints);
         const double* p = xy + (long long)h->dims * off;
-        const int rc = h->wide ? contract_round<true>(h, p, m) : contract_round<false>(h, p, m);
+        unsigned long long* k = keys_out ? keys_out + off : nullptr;
+        const int rc = h->wide ? contract_round<true>(h, p, m, k) : contract_round<false>(h, p, m, k);
         if (rc) return rc;
     }
     return RASTER_OK;
@@ -695,21 +697,24 @@ int ensure_label_index(raster_handle* h) {
     return RASTER_OK;
 }
 
-template <bool WIDE, int DIMS>
-void launch_labels(raster_handle* h, const double* xy, long long n, int64_t* labels) {
-    static int grid = grid_for((const void*)k_labels<WIDE, DIMS>, kBlock);
+// Labels of n points given by their coordinates (xy), or (KEYS) by the tile
+// keys that contraction stored for them.
+template <bool WIDE, int DIMS, bool KEYS = false>
+void launch_labels(raster_handle* h, const double* xy, long long n, int64_t* labels,
+                   const unsigned long long* keys = nullptr) {
+    static int grid = grid_for((const void*)k_labels<WIDE, DIMS, KEYS>, kBlock);
     LabelIndex li{nullptr, 0, 0, nullptr};
     if (DIMS == 2 && h->lidx_on)
         li = LabelIndex{h->lidx, h->lidx_buckets, h->lidx_share, reinterpret_cast<unsigned int*>(h->d_lidx + 1)};
     if (DIMS == 2 && h->lidx_on && kLabelsQueued) {
-        static int gq = grid_for((const void*)k_labels_idx<WIDE>, kBlock);
-        k_labels_idx<WIDE><<<(int)std::min<long long>(gq, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
-            xy, n, h->pp, table_of(h), reinterpret_cast<const long long*>(h->out_cid),
+        static int gq = grid_for((const void*)k_labels_idx<WIDE, KEYS>, kBlock);
+        k_labels_idx<WIDE, KEYS><<<(int)std::min<long long>(gq, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
+            xy, keys, n, h->pp, table_of(h), reinterpret_cast<const long long*>(h->out_cid),
             reinterpret_cast<long long*>(labels), h->d_status, li);
         return;
     }
-    k_labels<WIDE, DIMS><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
-        xy, n, h->pp, table_of(h), h->tau, reinterpret_cast<const long long*>(h->out_cid),
+    k_labels<WIDE, DIMS, KEYS><<<(int)std::min<long long>(grid, (n + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(
+        xy, keys, n, h->pp, table_of(h), h->tau, reinterpret_cast<const long long*>(h->out_cid),
         reinterpret_cast<long long*>(labels), h->d_status, li);
 }
 
@@ -930,6 +935,18 @@ int raster_contract(raster_handle* h, const double* xy, int64_t n, void* stream)
     return contract_device(h, xy, n);
 }
 
+int raster_contract_keys(raster_handle* h, const double* xy, int64_t n, int64_t* keys, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!xy || !keys || misaligned(xy, h->dims) || ((uintptr_t)keys & 7u))))
+        return RASTER_E_ARG;
+    if (hard_error(h->status)) return h->status;
+    if (h->points + n > 0xFFFFFFFFll) return RASTER_E_ARG;  // per-tile counts are 32-bit
+    h->stream = (cudaStream_t)stream;
+    h->state = raster_handle::kContracting;
+    h->points += n;
+    if (n == 0) return RASTER_OK;
+    return contract_device(h, xy, n, reinterpret_cast<unsigned long long*>(keys));
+}
+
 int raster_contract_host(raster_handle* h, const double* xy_host, int64_t n, void* stream) {
     if (!h || n < 0 || (n > 0 && !xy_host)) return RASTER_E_ARG;
     if (hard_error(h->status)) return h->status;
@@ -1056,6 +1073,25 @@ int raster_point_labels(raster_handle* h, const double* xy, int64_t n, int64_t* 
         h->wide ? launch_labels<true, 3>(h, xy, n, labels) : launch_labels<false, 3>(h, xy, n, labels);
     else
         h->wide ? launch_labels<true, 2>(h, xy, n, labels) : launch_labels<false, 2>(h, xy, n, labels);
+    note_launch();
+    RCHECK(h, cudaGetLastError());
+    return RASTER_OK;
+}
+
+int raster_key_labels(raster_handle* h, const int64_t* keys, int64_t n, int64_t* labels, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!keys || !labels || ((uintptr_t)keys & 7u) || ((uintptr_t)labels & 7u))))
+        return RASTER_E_ARG;
+    if (hard_error(h->status)) return h->status;
+    if (h->state != raster_handle::kAgglomerated) return RASTER_E_STATE;
+    h->stream = (cudaStream_t)stream;
+    if (n == 0) return RASTER_OK;
+    const int rc = ensure_label_index(h);
+    if (rc) return rc;
+    const unsigned long long* k = reinterpret_cast<const unsigned long long*>(keys);
+    if (h->dims == 3)
+        launch_labels<false, 3, true>(h, nullptr, n, labels, k);
+    else
+        launch_labels<false, 2, true>(h, nullptr, n, labels, k);
     note_launch();
     RCHECK(h, cudaGetLastError());
     return RASTER_OK;

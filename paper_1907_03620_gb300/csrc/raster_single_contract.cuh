@@ -21,7 +21,8 @@ __global__ void k_fill_table(Slot* tab, unsigned long long cap) {
 // each key's region beside it, as a 16-bit index), reserve space in each region's
 // staging segment with one atomic per (tile, region), and append the keys in
 // coalesced runs.  Keys beyond a segment's capacity (a region far above its
-// share) go to the overflow list.
+// share) go to the overflow list.  With keys_out, every point's key (or
+// kInvalidKey) is also stored there in point order, for the labels.
 constexpr int kPartTile = 2048;
 constexpr int kPartPer = kPartTile / kBlock;
 constexpr long long kInsertItem = 2048;
@@ -91,7 +92,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double* __restrict__ x
                                                 RegionTable t, unsigned long long* __restrict__ stage,
                                                 unsigned long long seg_cap, unsigned int* __restrict__ cursor,
                                                 unsigned long long* ovf_key, unsigned int* ovf_cnt,
-                                                unsigned long long* ovf_n, unsigned int* d_status) {
+                                                unsigned long long* ovf_n, unsigned int* d_status,
+                                                unsigned long long* __restrict__ keys_out) {
     extern __shared__ unsigned char smem[];
     unsigned long long* s_sorted = reinterpret_cast<unsigned long long*>(smem);         // kPartTile keys
     unsigned int* s_fill = reinterpret_cast<unsigned int*>(s_sorted + kPartTile);       // regions
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_part(const double* __restrict__ x
                 key[kk] = 0ull;
                 if (idx < n) {
                     key[kk] = project_in<WIDE, DIMS>(DIMS == 2 ? p[DIMS == 2 ? k : 0] : load_point<DIMS>(xy, idx), pp);
+                    if (keys_out) __stcs(keys_out + idx, key[kk]);  // each point's key, in point order
                     if (key[kk] == kInvalidKey) {
                         st |= kStRange;
                     } else {

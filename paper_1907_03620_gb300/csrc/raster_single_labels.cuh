@@ -214,15 +214,25 @@ __device__ __forceinline__ bool lidx_label(const LabelIndex& li, const RegionTab
     return lidx_label_from(li, key, bk, lidx_home(key, bk, t, li.share), kLidxProbe, lab);
 }
 
-template <bool WIDE, int DIMS>
-__global__ void k_labels(const double* __restrict__ xy, long long n, ProjParams pp, RegionTable t, unsigned int tau,
-                         const long long* __restrict__ cid_rows, long long* __restrict__ labels,
-                         unsigned int* d_status, LabelIndex li) {
+// The tile key of point i: projected from its coordinates, or (KEYS) read
+// from the keys that contraction stored for the same points.
+template <bool WIDE, int DIMS, bool KEYS>
+__device__ __forceinline__ unsigned long long point_key(const double* __restrict__ xy,
+                                                        const unsigned long long* __restrict__ keys, long long i,
+                                                        const ProjParams& pp) {
+    if (KEYS) return __ldcs(keys + i);
+    return project_in<WIDE, DIMS>(load_point<DIMS>(xy, i), pp);
+}
+
+template <bool WIDE, int DIMS, bool KEYS = false>
+__global__ void k_labels(const double* __restrict__ xy, const unsigned long long* __restrict__ keys, long long n,
+                         ProjParams pp, RegionTable t, unsigned int tau, const long long* __restrict__ cid_rows,
+                         long long* __restrict__ labels, unsigned int* d_status, LabelIndex li) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const bool use_index = DIMS == 2 && li.ent != nullptr && *li.bad == 0u;
     unsigned int st = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned long long key = project_in<WIDE, DIMS>(load_point<DIMS>(xy, i), pp);
+        const unsigned long long key = point_key<WIDE, DIMS, KEYS>(xy, keys, i, pp);
         long long lab = (long long)kEmptyKey;
         if (key == kInvalidKey) {
             st |= kStRange;
@@ -283,9 +293,11 @@ __device__ __forceinline__ int lidx_first(const LabelIndex& li, const RegionTabl
     return kLidxAnswered;
 }
 
-template <bool WIDE>
-__global__ void __launch_bounds__(kBlock) k_labels_idx(const double* __restrict__ xy, long long n, ProjParams pp,
-                                                      RegionTable t, const long long* __restrict__ cid_rows,
+template <bool WIDE, bool KEYS = false>
+__global__ void __launch_bounds__(kBlock) k_labels_idx(const double* __restrict__ xy,
+                                                      const unsigned long long* __restrict__ keys, long long n,
+                                                      ProjParams pp, RegionTable t,
+                                                      const long long* __restrict__ cid_rows,
                                                       long long* __restrict__ labels, unsigned int* d_status,
                                                       LabelIndex li) {
     __shared__ unsigned long long s_key[kBlock / 32][kLabQueue];
@@ -322,7 +334,7 @@ __global__ void __launch_bounds__(kBlock) k_labels_idx(const double* __restrict_
         bool defer = false, have = false;
         int mode = kLidxTable;
         if (i < n) {
-            key = project_in<WIDE, 2>(load_point<2>(xy, i), pp);
+            key = point_key<WIDE, 2, KEYS>(xy, keys, i, pp);
             if (key == kInvalidKey) {
                 st |= kStRange;
                 have = true;

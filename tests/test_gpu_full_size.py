@@ -117,3 +117,19 @@ def test_workload_500m_bit_exact():
     assert np.array_equal(k2[o2], sk) and np.array_equal(c2[o2], sc)
     a, b = res.sorted(), res2.sorted()
     assert torch.equal(a.key, b.key) and torch.equal(a.count, b.count) and torch.equal(a.cid, b.cid)
+    r2.close()
+    # 5. the key path of the bench step: one contract call that stores every point's key, then the
+    #    labels read from the keys -- the same table, kept rows and all 500M labels (checked above
+    #    against the oracle's digests), and sampled keys equal to the oracle's projection
+    r3 = R.Raster(w.precision, w.tau, w.mu)
+    keys = r3.contract_keys(d)
+    res3 = r3.agglomerate()
+    k3, c3 = r3.export_tiles()
+    k3, c3 = k3.cpu().numpy(), c3.cpu().numpy()
+    o3 = np.argsort(k3)
+    assert np.array_equal(k3[o3], sk) and np.array_equal(c3[o3], sc)
+    e = res3.sorted()
+    assert torch.equal(a.key, e.key) and torch.equal(a.count, e.count) and torch.equal(a.cid, e.cid)
+    assert torch.equal(r3.key_labels(keys), lab)
+    assert np.array_equal(keys[torch.from_numpy(idx).cuda()].cpu().numpy(), pk)
+    r3.close()
