@@ -113,7 +113,7 @@ struct raster_handle {
     // [6] keys refused by a full bucket
     unsigned long long* d_ctr = nullptr;
     unsigned int* d_status = nullptr;
-    unsigned long long* h_ctr = nullptr;  // pinned mirror: 7 counters, then the status word
+    unsigned long long* h_ctr = nullptr;  // pinned mirror: 8 counters, then the status word
 
     // agglomeration scratch and results (capacity in rows)
     long long agg_cap = 0;
@@ -152,6 +152,10 @@ struct raster_handle {
     // the table's contents are void (after a reset): the next contraction
     // round starts its buckets empty instead of reading them
     bool fresh = false;
+    // the significant tiles were selected while the last round wrote the
+    // table (k_insert_fresh): rows in sig_key/sig_cnt/sig_slot, their count in
+    // d_ctr[7], aux set; valid until the table changes again
+    bool presel = false;
 
     unsigned long long* d_work = nullptr;  // work counters of the ordered kernels (8)
 
@@ -257,11 +261,11 @@ int fill_table(raster_handle* h, Slot* tab, unsigned long long cap, cudaStream_t
 
 // Read the device counters and status into h_ctr (synchronises the stream).
 int read_counters(raster_handle* h) {
-    RCHECK(h, cudaMemcpyAsync(h->h_ctr, h->d_ctr, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
-    h->h_ctr[7] = 0;
-    RCHECK(h, cudaMemcpyAsync(h->h_ctr + 7, h->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+    RCHECK(h, cudaMemcpyAsync(h->h_ctr, h->d_ctr, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    h->h_ctr[8] = 0;
+    RCHECK(h, cudaMemcpyAsync(h->h_ctr + 8, h->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
     RCHECK(h, cudaStreamSynchronize(h->stream));
-    merge_status(h, status_from_bits((unsigned int)h->h_ctr[7]));
+    merge_status(h, status_from_bits((unsigned int)h->h_ctr[8]));
     return RASTER_OK;
 }
 
@@ -270,6 +274,7 @@ int grow_table(raster_handle* h, unsigned int regions, unsigned int bits) {
     // capacity is at most 2^32 slots, so at most 4096 regions: k_part keeps
     // region indices in 16 bits
     if (regions > 0xFFFFu) return RASTER_E_OOM;
+    h->presel = false;  // slots move
     const unsigned long long new_cap = (unsigned long long)regions << bits;
     Slot* nt = nullptr;
     RCHECK(h, cudaMalloc(&nt, new_cap * sizeof(Slot)));
@@ -397,6 +402,7 @@ constexpr double kRefitRatio = 1.5;              // a grown table this much larg
 constexpr double kPreGrow = 4.0;                 // grow before a round whose estimate is this far past kMaxLoad
 constexpr bool kLabelsQueued = true;             // labels with the block index: k_labels_idx (queued fallbacks)
 constexpr bool kInsertSplit = true;              // pass 2 into a void table: split key/count buckets (k_insert_fresh)
+constexpr bool kPreSelect = true;                // k_insert_fresh selects the significant tiles as it writes
 
 // One contraction round of n points: pass 1, item prefix, pass 1b, pass 2
 // (all asynchronous), then one synchronisation to read the table's tile count
@@ -411,6 +417,7 @@ int round_begin(raster_handle* h, long long n) {
     // smaller in round_finish.
     int rc;
     h->round_grew = false;
+    h->presel = false;  // this round changes counts; round_finish may select again
     const double est = (double)h->d_bound + 0.5 * (double)n;
     if (est > kPreGrow * kMaxLoad * (double)h->cap) {
         unsigned int regions, bits;
@@ -461,6 +468,7 @@ int round_part(raster_handle* h, const double* xy, long long m, unsigned long lo
 int round_finish(raster_handle* h, long long n) {
     int rc;
     const bool grew_before = h->round_grew;
+    bool presel_tried = false;
     const unsigned long long seg = (h->stage_cap / h->regions) & ~1ull;  // even: 16-byte aligned item starts
     RegionTable t = table_of(h);
     k_region_items<<<1, kBlock, 0, h->stream>>>(h->cursor, (int)h->regions, seg, h->item_start);
@@ -518,11 +526,20 @@ int round_finish(raster_handle* h, long long n) {
         k_bucket<<<gb, kBlock, kBucketSmem, h->stream>>>(t, h->stage_keys, seg, h->cursor, h->item_start, (int)h->regions,
                                                          h->stage2, seg2, h->bcursor, h->ovf_key, h->ovf_cnt,
                                                          h->d_ctr + 5, h->d_work);
+        // the selection of significant tiles rides along when the rows have
+        // room (the 2 x 2 group rule marks tiles first, so it selects later)
+        presel_tried = kInsertSplit && h->fresh && kPreSelect && !h->groups && h->agg_cap > 0;
+        PreSelect sel{0u, nullptr, nullptr, nullptr, nullptr, 0ull};
+        if (presel_tried) {
+            RCHECK(h, cudaMemsetAsync(h->d_ctr + 7, 0, sizeof(unsigned long long), h->stream));
+            sel = PreSelect{h->tau, h->sig_key, h->sig_cnt, h->sig_slot, h->d_ctr + 7,
+                            (unsigned long long)h->agg_cap};
+        }
         if (kInsertSplit && h->fresh)
             ins_fresh<<<(int)std::min<unsigned long long>((unsigned long long)gf, n_buckets), kInsBlock, fsmem,
                         h->stream>>>(h->tab, n_buckets, h->stage2, seg2, h->bcursor,
                                      (unsigned int)(kNewLimit * kBucketSlots), probe, h->d_ctr, h->d_ctr + 6,
-                                     h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work + 1);
+                                     h->ovf_key, h->ovf_cnt, h->d_ctr + 5, h->d_work + 1, sel);
         else
             ins<<<(int)std::min<unsigned long long>((unsigned long long)gi, n_buckets), kInsBlock, bsmem, h->stream>>>(
                 h->tab, n_buckets, h->stage2, seg2, h->bcursor, h->fresh ? 1 : 0,
@@ -535,6 +552,9 @@ int round_finish(raster_handle* h, long long n) {
     rc = read_counters(h);
     if (rc) return rc;
     const unsigned long long D = h->h_ctr[0], ovf = h->h_ctr[5], full = h->h_ctr[6];
+    // the selection holds only if no count or slot changes after it: no
+    // overflow to re-insert, no growth before or after, every row written
+    const bool presel_ok = presel_tried && !grew_before && ovf == 0 && h->h_ctr[7] <= (unsigned long long)h->agg_cap;
     // D + ovf bounds the tile count; a bucket that refused new tiles needs room too
     bool grew = grew_before;
     if ((double)(D + ovf) > kMaxLoad * (double)h->cap || full > 0) {
@@ -567,6 +587,7 @@ int round_finish(raster_handle* h, long long n) {
         if (rc) return rc;
     }
     h->d_bound = (long long)h->h_ctr[0];
+    h->presel = presel_ok && !grew;
     return RASTER_OK;
 }
 
@@ -855,7 +876,7 @@ int raster_create_ex(const raster_params* params, raster_handle** out) {
     cudaError_t e = cudaMalloc(&h->d_ctr, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_work, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctr, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctr, 9 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_nbr, sizeof(NbrSet));
@@ -910,6 +931,7 @@ int raster_contract_tiles(raster_handle* h, const int64_t* key, const uint32_t* 
     rc = ensure_clean(h);
     if (rc) return rc;
     h->state = raster_handle::kContracting;
+    h->presel = false;  // counts change
     h->points += (long long)points;
     RegionTable t = table_of(h);
     t.max_probe = insert_probe(h, t.max_probe);
@@ -1000,6 +1022,10 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
     if (D >= 0x7FFFFFFFll) return RASTER_E_OOM;
     rc = ensure_clean(h);
     if (rc) return rc;
+    // the significant tiles selected during contraction, unless the row
+    // buffers are about to be replaced by larger ones
+    const bool presel = h->presel && !h->groups && std::max<long long>(D, 1) <= h->agg_cap;
+    h->presel = false;  // the aux fields are rewritten below
     rc = ensure_agg_capacity(h, std::max<long long>(D, 1));
     if (rc) return rc;
     cudaStream_t s = h->stream;
@@ -1012,11 +1038,16 @@ int raster_agglomerate(raster_handle* h, raster_clusters* out) {
         k_groups<<<g_grp, kBlock, 0, s>>>(h->tab, table_of(h), h->tau, h->d_work + 6);
         note_launch();
     }
-    RCHECK(h, cudaMemsetAsync(h->d_work + 3, 0, sizeof(unsigned long long), s));
-    k_select<<<g_sel, kBlock, 0, s>>>(h->tab, h->cap, h->tau, h->sig_key, h->sig_cnt, h->sig_slot, d_nsig,
-                                      (unsigned long long)h->agg_cap, 1, h->groups ? 1 : 0, h->d_work + 3);
+    if (presel) {
+        RCHECK(h, cudaMemcpyAsync(d_nsig, h->d_ctr + 7, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+    } else {
+        RCHECK(h, cudaMemsetAsync(h->d_work + 3, 0, sizeof(unsigned long long), s));
+        k_select<<<g_sel, kBlock, 0, s>>>(h->tab, h->cap, h->tau, h->sig_key, h->sig_cnt, h->sig_slot, d_nsig,
+                                          (unsigned long long)h->agg_cap, 1, h->groups ? 1 : 0, h->d_work + 3);
+        note_launch();
+    }
     k_clamp_rows<<<1, 1, 0, s>>>(d_nsig, (unsigned long long)h->agg_cap, h->d_status);
-    note_launch(2);
+    note_launch();
     RCHECK(h, cudaGetLastError());
     static int g_init = grid_for((const void*)k_uf_init, kBlock);
     static int g_hook = grid_for((const void*)k_hook<false>, kBlock);
@@ -1323,6 +1354,7 @@ int raster_reset(raster_handle* h, void* stream) {
     // the table's contents become void; the next contraction round writes
     // every bucket, and any other reader fills the table first
     h->fresh = true;
+    h->presel = false;
     RCHECK(h, cudaMemsetAsync(h->d_ctr, 0, 8 * sizeof(unsigned long long), h->stream));
     RCHECK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned int), h->stream));
     h->d_bound = 0;

@@ -477,21 +477,37 @@ __global__ void __launch_bounds__(kInsBlock) k_insert_bucket(Slot* __restrict__ 
 // k_insert_bucket, but the bucket is cleared rather than loaded, and held as
 // separate key and count arrays (48 KiB instead of 64 KiB: four blocks of
 // kInsBlock threads per SM instead of three); it is written back as whole
-// slots with aux none.  Every bucket is written, so the table needs no fill.
+// slots.  Every bucket is written, so the table needs no fill.
+// With sel.tau > 0 it also selects the significant tiles (count >= tau) of
+// each bucket as it writes it back, as the agglomeration's selection would
+// (Alg. 1 second loop): their (key, count, slot) rows go to sel, and each
+// such slot's aux gets its row (every other slot: aux none).  The counts are
+// final for the round when the bucket is written; whether no later insertion
+// changed them (overflow, growth, another round) is the host's to check.
+struct PreSelect {
+    unsigned int tau;  // 0: no selection
+    unsigned long long* key;
+    unsigned int* cnt;
+    unsigned int* slot;
+    unsigned long long* n;  // rows selected (may exceed cap: rows beyond it are not written)
+    unsigned long long cap;
+};
 template <bool LIMITED>
 __global__ void __launch_bounds__(kInsBlock, 4)
     k_insert_fresh(Slot* __restrict__ tab, unsigned long long n_buckets, const unsigned long long* __restrict__ stage2,
                    unsigned long long seg2, const unsigned int* __restrict__ bcursor, unsigned int limit,
                    unsigned int max_probe, unsigned long long* d_newkeys, unsigned long long* d_full,
                    unsigned long long* ovf_key, unsigned int* ovf_cnt, unsigned long long* ovf_n,
-                   unsigned long long* work) {
+                   unsigned long long* work, PreSelect sel) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* s_key = reinterpret_cast<unsigned long long*>(smem);     // kBucketSlots keys
     unsigned int* s_cnt = reinterpret_cast<unsigned int*>(s_key + kBucketSlots);  // kBucketSlots counts
     __shared__ unsigned int s_occ, s_nfull;
     __shared__ int s_full;
-    __shared__ unsigned long long s_b;
+    __shared__ unsigned long long s_b, s_row;
+    __shared__ unsigned int scratch[33];
     const int lane = threadIdx.x & 31;
+    constexpr int kPairs = (int)(kBucketSlots / 2 / kInsBlock);  // slot pairs per thread in the write-back
     for (;;) {
         // the previous bucket's write-back ended at a barrier
         if (threadIdx.x == 0) {
@@ -539,17 +555,57 @@ __global__ void __launch_bounds__(kInsBlock, 4)
         full = __reduce_add_sync(0xFFFFFFFFu, full);
         if (lane == 0 && full) atomicAdd(&s_nfull, full);
         __syncthreads();
+        // significant slots of the bucket: bit 2k (2k+1) for the first (second)
+        // slot of the thread's k-th pair; their rows, in the thread's order
+        unsigned int sig = 0;
+        unsigned long long row = 0;
+        if (sel.tau) {  // block-uniform
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k) {
+                const unsigned int i = threadIdx.x + (unsigned int)k * kInsBlock;
+                const ulonglong2 k2 = reinterpret_cast<const ulonglong2*>(s_key)[i];
+                const uint2 c2 = reinterpret_cast<const uint2*>(s_cnt)[i];
+                sig |= (unsigned int)(k2.x != kEmptyKey && c2.x >= sel.tau) << (2 * k);
+                sig |= (unsigned int)(k2.y != kEmptyKey && c2.y >= sel.tau) << (2 * k + 1);
+            }
+            unsigned int total;
+            const unsigned int off = block_excl_scan<kInsBlock>((unsigned int)__popc(sig), scratch, &total);
+            if (threadIdx.x == 0) s_row = total ? atomicAdd(sel.n, (unsigned long long)total) : 0ull;
+            __syncthreads();
+            row = s_row + off;
+        }
         // two slots per thread and step: one 16-byte and one 8-byte shared load, two 16-byte stores
         ulonglong2* g = reinterpret_cast<ulonglong2*>(tab + (b << kBucketBits));
         unsigned int occ = 0;
-        for (unsigned int i = threadIdx.x; i < kBucketSlots / 2; i += kInsBlock) {
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+            const unsigned int i = threadIdx.x + (unsigned int)k * kInsBlock;
             const ulonglong2 k2 = reinterpret_cast<const ulonglong2*>(s_key)[i];
             const uint2 c2 = reinterpret_cast<const uint2*>(s_cnt)[i];
+            unsigned int aux0 = kAuxNone, aux1 = kAuxNone;
+            if (sig & (1u << (2 * k))) {
+                if (row < sel.cap) {
+                    aux0 = (unsigned int)row;
+                    sel.key[row] = k2.x;
+                    sel.cnt[row] = c2.x;
+                    sel.slot[row] = (unsigned int)((b << kBucketBits) + 2 * i);
+                }
+                ++row;
+            }
+            if (sig & (2u << (2 * k))) {
+                if (row < sel.cap) {
+                    aux1 = (unsigned int)row;
+                    sel.key[row] = k2.y;
+                    sel.cnt[row] = c2.y;
+                    sel.slot[row] = (unsigned int)((b << kBucketBits) + 2 * i + 1);
+                }
+                ++row;
+            }
             ulonglong2 v0, v1;
             v0.x = k2.x;
-            v0.y = ((unsigned long long)kAuxNone << 32) | c2.x;
+            v0.y = ((unsigned long long)aux0 << 32) | c2.x;
             v1.x = k2.y;
-            v1.y = ((unsigned long long)kAuxNone << 32) | c2.y;
+            v1.y = ((unsigned long long)aux1 << 32) | c2.y;
             occ += (k2.x != kEmptyKey) + (k2.y != kEmptyKey);
             g[2 * i] = v0;
             g[2 * i + 1] = v1;

@@ -132,4 +132,12 @@ def test_workload_500m_bit_exact():
     assert torch.equal(a.key, e.key) and torch.equal(a.count, e.count) and torch.equal(a.cid, e.cid)
     assert torch.equal(r3.key_labels(keys), lab)
     assert np.array_equal(keys[torch.from_numpy(idx).cuda()].cpu().numpy(), pk)
+    # 6. the bench's steady step: reset, one round that also selects the significant tiles as it
+    #    writes the table, agglomeration from that selection, labels from the keys
+    for _ in range(2):
+        r3.reset()
+        r3.contract_keys(d, keys)
+        f = r3.agglomerate().sorted()
+        assert torch.equal(a.key, f.key) and torch.equal(a.count, f.count) and torch.equal(a.cid, f.cid)
+        assert torch.equal(r3.key_labels(keys), lab)
     r3.close()

@@ -99,6 +99,16 @@ def test_workload_1m_bit_exact():
     r, res, lab = gpu_run(xy, w.precision, w.tau, w.mu)
     assert_same(res, lab, ref, ref_lab)
     assert ref.n_clusters > 900
+    # a second cycle on the same handle: the one round after the reset selects
+    # the significant tiles as it writes the table, and the agglomeration uses
+    # that selection instead of scanning the table
+    d = torch.from_numpy(xy).cuda()
+    for _ in range(2):
+        r.reset()
+        r.contract(d)
+        assert_same(r.agglomerate(), r.point_labels(d).cpu().numpy(), ref, ref_lab)
+    # agglomerating twice: the second one scans the table (the first rewrote aux)
+    assert_same(r.agglomerate(), r.point_labels(d).cpu().numpy(), ref, ref_lab)
 
 
 @pytest.mark.parametrize("seed", range(8))
@@ -212,6 +222,12 @@ def test_skewed_regions_spill_to_overflow_list():
     res = r.agglomerate()
     assert r.capacity == cap  # spilling alone does not grow the table
     assert_same(res, r.point_labels(d).cpu().numpy(), ref, ref_lab)
+    # one round after a reset, with spilled keys re-inserted after the buckets
+    # were written: the selection made while writing them must not be used
+    r.reset()
+    r.contract(d)
+    assert r.capacity == cap
+    assert_same(r.agglomerate(), r.point_labels(d).cpu().numpy(), ref, ref_lab)
 
 
 def test_host_buffer_variants():
