@@ -43,12 +43,13 @@ POINT_BYTES = 16         # algorithmic bytes per point (x, y read once)
 # its reset) in a steady-state step, from one ncu capture
 # with one pass per launch on the 100M-point case of the same workload
 # (`--points 100000000`: 1.6 GB of points, a 91M-slot table).  The traffic
-# grows with the points (16 B read, keys staged twice) and with the table
-# slots (each written once), so it scales to a full launch as
+# grows with the points (16 B read, each point's key stored, keys staged
+# twice) and with the table slots (each written once, with the selected
+# significant rows beside them), so it scales to a full launch as
 # per_point * n + per_slot * slots.  Valid only for the contraction kernels'
 # sources it was measured with (their digest); reported as null otherwise.
-MEASURED_CONTRACT_TRAFFIC = {"sources": "6f1a362e440c8355", "case_points": 100_000_000, "case_slots": 91_226_112,
-                             "per_point": 4.749e9 / 100_000_000, "per_slot": 1.394e9 / 91_226_112}
+MEASURED_CONTRACT_TRAFFIC = {"sources": "42f19a62f49a1162", "case_points": 100_000_000, "case_slots": 91_226_112,
+                             "per_point": 5.515e9 / 100_000_000, "per_slot": 1.549e9 / 91_226_112}
 
 
 def kernel_sources_digest() -> str:
